@@ -1,0 +1,146 @@
+"""CPU oracle — TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, obviously correct CPU implementations of what the GPU library
+computes, used by the tests, the smoke check and the benchmark's CPU-baseline
+leg, and by nothing else. The GPU product path never imports this package.
+
+* ``pregel.c`` — a single-threaded synchronous Pregel engine (Section 4.2,
+  Fig. 3; vertex selection of Section 4.3.1; combined one-slot mailboxes of
+  Section 4.3.3) running PageRank (Fig. 8 with the Pregel constant of
+  Fig. 12), Hashmin (Fig. 9) and weighted SSSP (Fig. 10 with per-edge
+  weights). PageRank runs in FP64.
+* ``mlp.py`` — FP64 forward/backward of the 8-32-32-3 mode-selector MLP.
+
+The compiled part is built on first use with gcc (``build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pregel.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+INF = 0xFFFFFFFF
+
+U32 = ctypes.POINTER(ctypes.c_uint32)
+U64 = ctypes.POINTER(ctypes.c_uint64)
+F64 = ctypes.POINTER(ctypes.c_double)
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("supersteps", ctypes.c_uint32), ("halted", ctypes.c_int32), ("cap", ctypes.c_uint32),
+                ("active", U32), ("broadcasters", U32), ("messages", U64)]
+
+
+def build(force: bool = False) -> str:
+    """Compile pregel.c into liboracle.so (single-threaded, -O2)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp], check=True,
+                   capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            st = ctypes.POINTER(_Stats)
+            lib.oracle_pagerank.argtypes = [ctypes.c_uint32, U32, U32, ctypes.c_uint32, ctypes.c_double,
+                                            ctypes.c_uint32, F64, st]
+            lib.oracle_hashmin.argtypes = [ctypes.c_uint32, U32, U32, ctypes.c_uint32, U32, st]
+            lib.oracle_sssp.argtypes = [ctypes.c_uint32, U32, U32, U32, ctypes.c_uint32, ctypes.c_uint32, U32, st]
+            for f in (lib.oracle_pagerank, lib.oracle_hashmin, lib.oracle_sssp):
+                f.restype = ctypes.c_int
+            _lib = lib
+        return _lib
+
+
+def _u32(a):
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    if a.size == 0:
+        a = np.zeros(1, np.uint32)
+    return a
+
+
+def _stats(cap):
+    act = np.zeros(max(cap, 1), np.uint32)
+    bc = np.zeros(max(cap, 1), np.uint32)
+    msg = np.zeros(max(cap, 1), np.uint64)
+    s = _Stats(0, 0, cap, act.ctypes.data_as(U32), bc.ctypes.data_as(U32), msg.ctypes.data_as(U64))
+    return s, (act, bc, msg)
+
+
+def _finish(r, s, arrs):
+    if r < 0:
+        raise MemoryError("oracle allocation failed")
+    n = min(s.supersteps, s.cap)
+    act, bc, msg = arrs
+    return dict(supersteps=int(s.supersteps), halted=bool(s.halted), active=act[:n].copy(),
+                broadcasters=bc[:n].copy(), messages=msg[:n].copy())
+
+
+def pagerank(n, row_ptr, col, T=30, damping=0.85, max_supersteps=None, stats_cap=None):
+    """FP64 synchronous-Pregel PageRank (Fig. 8). Returns (rank[n] float64, stats)."""
+    if max_supersteps is None:
+        max_supersteps = T + 1
+    cap = max_supersteps if stats_cap is None else stats_cap
+    out = np.zeros(max(n, 1), np.float64)
+    s, arrs = _stats(cap)
+    r = _L().oracle_pagerank(n, _u32(row_ptr).ctypes.data_as(U32), _u32(col).ctypes.data_as(U32), T,
+                             float(damping), max_supersteps, out.ctypes.data_as(F64), ctypes.byref(s))
+    return out[:n], _finish(r, s, arrs)
+
+
+def hashmin(n, row_ptr, col, max_supersteps=1 << 30, stats_cap=4096):
+    """Hashmin labels (Fig. 9). Returns (label[n] uint32, stats)."""
+    out = np.zeros(max(n, 1), np.uint32)
+    s, arrs = _stats(stats_cap)
+    rp, c = _u32(row_ptr), _u32(col)
+    r = _L().oracle_hashmin(n, rp.ctypes.data_as(U32), c.ctypes.data_as(U32), max_supersteps,
+                            out.ctypes.data_as(U32), ctypes.byref(s))
+    return out[:n], _finish(r, s, arrs)
+
+
+def sssp(n, row_ptr, col, w=None, source=0, max_supersteps=1 << 30, stats_cap=4096):
+    """SSSP distances (Fig. 10, message = value + w(u,v), INF = 0xFFFFFFFF). Returns (dist, stats)."""
+    out = np.zeros(max(n, 1), np.uint32)
+    s, arrs = _stats(stats_cap)
+    rp, c = _u32(row_ptr), _u32(col)
+    wp = _u32(w).ctypes.data_as(U32) if w is not None else None
+    r = _L().oracle_sssp(n, rp.ctypes.data_as(U32), c.ctypes.data_as(U32), wp, source, max_supersteps,
+                         out.ctypes.data_as(U32), ctypes.byref(s))
+    return out[:n], _finish(r, s, arrs)
+
+
+def run_app(app: str, g, **kw):
+    """Dispatch on an app name for a graph object with row_ptr/col/w/n."""
+    if app == "pagerank":
+        return pagerank(g.n, g.row_ptr, g.col, **kw)
+    if app == "hashmin":
+        return hashmin(g.n, g.row_ptr, g.col, **kw)
+    if app == "sssp":
+        return sssp(g.n, g.row_ptr, g.col, g.w, **kw)
+    raise ValueError(app)
+
+
+def batch_sssp(g, sources, **kw):
+    """Independent SSSP runs, one per source: dist[k, n] (source-major)."""
+    return np.stack([sssp(g.n, g.row_ptr, g.col, g.w, int(s), **kw)[0] for s in sources]) if len(sources) \
+        else np.zeros((0, g.n), np.uint32)
+
+
+def batch_hashmin(graphs):
+    """Hashmin on each graph separately: list of label arrays (local vertex IDs)."""
+    return [hashmin(h.n, h.row_ptr, h.col)[0] for h in graphs]
