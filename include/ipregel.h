@@ -1,0 +1,191 @@
+/*
+ * ipregel.h — C ABI of the GB300 (sm_103a) synchronous vertex-centric superstep
+ * library (libipregel_gb300.so).
+ *
+ * The library runs the superstep model of the iPregel paper (Capelli et al.,
+ * "iPregel: Vertex-centric programmability vs memory efficiency and
+ * performance, why choose?", Parallel Computing 2019): Section 4.2 and Fig. 3
+ * (bulk-synchronous supersteps: compute, communicate, synchronise), with the
+ * optimisations of Section 4.3 (selection bypass, push or pull message
+ * exchange, combined one-slot mailboxes) for its three applications:
+ * PageRank (Fig. 8, sum combiner), Hashmin connected components (Fig. 9, min
+ * combiner) and single-source shortest paths (Fig. 10, min combiner, here with
+ * per-edge uint32 weights).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns int: IP_OK (0) or a negative IP_E_* code. No C++
+ *    exception crosses this boundary.
+ *  - Vertex IDs are uint32 in [0, n_vertices); edge offsets are uint32, so a
+ *    graph holds at most 2^32 - 1 directed edges.
+ *  - An ip_graph_t owns all device memory it uses. Caller buffers are only read
+ *    (or written, for outputs) during the call and never retained.
+ *  - `stream` arguments are cudaStream_t values passed as void*; NULL means the
+ *    legacy default stream. Calls that return results synchronise that stream
+ *    before returning.
+ *  - Handles are not thread safe: one thread at a time per handle.
+ */
+#ifndef IPREGEL_H
+#define IPREGEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define IP_OK 0
+#define IP_E_INVAL (-1)         /* malformed argument or graph (offsets, sizes, NULL) */
+#define IP_E_RANGE (-2)         /* a vertex ID, size or count out of range */
+#define IP_E_NOMEM (-3)         /* a device allocation failed */
+#define IP_E_CUDA (-4)          /* a CUDA runtime call failed */
+#define IP_E_TIMEOUT (-5)       /* a bounded device-side wait gave up */
+#define IP_E_MAXSTEPS (-6)      /* the superstep cap stopped the run before global halt;
+                                   the values hold the state after the last superstep run */
+#define IP_E_DEVICE_ASSERT (-7) /* a device-side check recorded an error */
+#define IP_E_STATE (-8)         /* the call is not valid in the handle's current state */
+
+/* ------------------------------------------------------------ enumerations */
+typedef enum {
+    IP_PAGERANK = 0, /* Fig. 8 (constant (1-d)/N as in Fig. 12); FP32 ranks */
+    IP_HASHMIN = 1,  /* Fig. 9; uint32 labels */
+    IP_SSSP = 2      /* Fig. 10 with message value(u) + w(u,v); uint32 distances,
+                        unreachable = 0xFFFFFFFF */
+} ip_app_t;
+
+/* How the messages broadcast in superstep s reach their recipients in s+1
+ * (Section 4.3.2): pushed along out-edges by the senders, from a compacted
+ * queue of senders (PUSH_SPARSE, the selection bypass of Section 4.3.1) or by
+ * scanning a sender bitmap over all vertices (PUSH_DENSE); or pulled by every
+ * vertex from its in-neighbours' broadcast values (PULL). The vertex values
+ * after every superstep do not depend on the mode. */
+typedef enum { IP_MODE_PUSH_SPARSE = 0, IP_MODE_PUSH_DENSE = 1, IP_MODE_PULL = 2 } ip_mode_t;
+
+typedef enum {
+    IP_POLICY_AUTO = 0,      /* the learned selector if one is loaded, else the threshold rule */
+    IP_POLICY_THRESHOLD = 1, /* fixed rule on the frontier's out-edge fraction (see ip_options_t) */
+    IP_POLICY_MLP = 2,       /* the learned selector; IP_E_STATE if none is loaded */
+    IP_POLICY_FORCED = 3,    /* always forced_mode */
+    IP_POLICY_SEQUENCE = 4   /* exchange into superstep s uses mode_sequence[(s-1) % len] */
+} ip_policy_t;
+
+typedef struct ip_graph ip_graph_t;
+
+/* Options of one run. Fill with ip_options_default() and override fields. */
+typedef struct {
+    float damping;                /* PageRank damping d (default 0.85) */
+    uint32_t pr_iterations;       /* PageRank T: broadcasts while superstep < T (default 30) */
+    uint32_t source;              /* SSSP source vertex (default 0) */
+    int32_t policy;               /* ip_policy_t (default IP_POLICY_AUTO) */
+    int32_t forced_mode;          /* ip_mode_t for IP_POLICY_FORCED */
+    const uint8_t* mode_sequence; /* host array of ip_mode_t for IP_POLICY_SEQUENCE */
+    uint32_t mode_sequence_len;   /* 1..64 */
+    uint32_t t1;                  /* degree cutoff: deg <= t1 is handled by one lane (0 = default) */
+    uint32_t t2;                  /* degree cutoff: deg >= t2 is handled by a whole CTA (0 = default);
+                                     between the two a warp handles the vertex */
+    float thr_sparse;             /* threshold rule: f = out-edges of senders / E; f < thr_sparse
+                                     -> PUSH_SPARSE, f >= thr_pull -> PULL, else PUSH_DENSE */
+    float thr_pull;
+    int32_t use_graph;            /* 1 (default): the whole run is one CUDA graph whose superstep
+                                     loop runs on the device (conditional while/switch nodes);
+                                     0: the host drives the loop, one 4-byte readback per superstep */
+    int32_t collect_labels;       /* 1: also time all three modes in every superstep (host loop);
+                                     fills ip_run_stats_t.mode_ms. Values are unchanged. */
+    void* stream;                 /* cudaStream_t */
+} ip_options_t;
+
+/* Per-run statistics. The caller owns the arrays; `capacity` is their length in
+ * supersteps (entries for supersteps >= capacity are dropped). Any array
+ * pointer may be NULL. */
+typedef struct {
+    uint32_t supersteps;   /* supersteps executed, superstep 0 included */
+    int32_t halted;        /* 1: global halt; 0: the cap stopped the run */
+    uint32_t capacity;
+    uint8_t* mode;         /* [s]: mode that delivered the messages read in superstep s
+                              (255 for superstep 0) */
+    uint32_t* active;      /* [s]: vertices that ran compute() in superstep s */
+    uint32_t* broadcasters;/* [s]: vertices that broadcast in superstep s */
+    uint64_t* messages;    /* [s]: messages sent in superstep s */
+    float* features;       /* [8*s + i]: selector input computed after superstep s */
+    float* mode_ms;        /* [3*s + m]: milliseconds of mode m delivering into superstep s
+                              (collect_labels only; 0 otherwise) */
+    float elapsed_ms;      /* device time of the whole run (init to halt) */
+} ip_run_stats_t;
+
+/* Graph facts for callers and tests. */
+typedef struct {
+    uint32_t n_vertices;
+    uint64_t n_edges;
+    uint32_t max_out_degree;
+    uint32_t max_in_degree;
+    uint32_t csc_is_csr;      /* 1 when the in-edge arrays alias the out-edge arrays */
+    uint32_t weighted;
+    uint32_t num_sms;         /* SMs of the device the graph lives on */
+    uint64_t device_bytes;    /* device memory held by the handle */
+} ip_graph_info_t;
+
+/* ------------------------------------------------------------ entry points */
+
+/* Sets every field of *opt to its default. */
+void ip_options_default(ip_options_t* opt);
+
+/* Creates a graph on the current CUDA device (Section 4.2: the vertex array and
+ * the adjacency array of the paper become a CSR (out-edges) and a CSC (in-edges)
+ * store).
+ *   n_vertices   >= 1.
+ *   n_edges      number of directed edges, < 2^32.
+ *   csr_offsets  n_vertices+1 offsets (offsets[0] = 0, non-decreasing,
+ *                offsets[n] = n_edges); csr_cols n_edges destination IDs.
+ *   csr_weights  n_edges weights in CSR order, or NULL (unweighted: every
+ *                edge weighs 1 for SSSP).
+ *   csc_offsets / csc_rows / csc_weights  the in-edge (transposed) arrays in the
+ *                same form; NULL csc_offsets means "build the transpose on the
+ *                device"; csc_offsets == csr_offsets and csc_rows == csr_cols
+ *                declares a symmetric graph and shares the arrays. csc_weights
+ *                is required when csc arrays and csr_weights are both given.
+ *   device_ptrs  0: all arrays are host memory; 1: all are device memory.
+ * Host arrays are validated on the host (IP_E_INVAL / IP_E_RANGE); device
+ * arrays by a device check (same codes). The library copies every array.
+ * A CSC that is not the transpose of the CSR is not detected: pull mode then
+ * computes on the CSC's edges. */
+int ip_graph_create(ip_graph_t** out, uint32_t n_vertices, uint64_t n_edges, const uint32_t* csr_offsets,
+                    const uint32_t* csr_cols, const uint32_t* csr_weights, const uint32_t* csc_offsets,
+                    const uint32_t* csc_rows, const uint32_t* csc_weights, int device_ptrs, void* stream);
+
+/* Frees every device buffer of the handle. NULL is ignored. */
+void ip_graph_destroy(ip_graph_t* g);
+
+int ip_graph_info(const ip_graph_t* g, ip_graph_info_t* info);
+
+/* Runs one application to global halt (Section 4.2: the run ends when every
+ * vertex has voted to halt and no message is in flight) or until
+ * max_supersteps supersteps (superstep 0 included) have run, whichever comes
+ * first; returns IP_E_MAXSTEPS in the second case. PageRank halts after
+ * superstep T = opt->pr_iterations (T+1 supersteps). opt may be NULL
+ * (defaults). stats may be NULL. The values stay on the device until
+ * ip_get_values or the next run. */
+int ip_run(ip_graph_t* g, ip_app_t app, uint32_t max_supersteps, const ip_options_t* opt,
+           ip_run_stats_t* stats);
+
+/* Copies the values of the last run: n_vertices FP32 ranks (PageRank) or
+ * uint32 labels / distances. dst_bytes must be >= 4 * n_vertices.
+ * IP_E_STATE if nothing has run yet. */
+int ip_get_values(ip_graph_t* g, void* dst, size_t dst_bytes, int dst_is_device, void* stream);
+
+/* Loads the learned mode selector (a trained 8-32-32-3 MLP) into the handle.
+ * blob layout (little endian, IP_SELECTOR_BYTES bytes):
+ *   float  mu[8], sd[8]          feature normalisation
+ *   bf16   W1[32][8], W2[32][32], W3[3][32]   (row-major, output-major)
+ *   float  b1[32], b2[32], b3[3]
+ * bytes must equal IP_SELECTOR_BYTES. */
+#define IP_SELECTOR_BYTES (16 * 4 + (32 * 8 + 32 * 32 + 3 * 32) * 2 + (32 + 32 + 3) * 4)
+int ip_set_selector(ip_graph_t* g, const void* blob, size_t bytes);
+
+/* Human-readable text for an IP_* code (static storage). */
+const char* ip_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPREGEL_H */

@@ -1,0 +1,280 @@
+"""Python binding of libipregel_gb300.so (the C ABI declared in include/ipregel.h).
+
+Argument marshalling only: every superstep runs in the library's CUDA kernels.
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device memory);
+PyTorch supplies device memory and streams, nothing else. There is no CPU
+fallback: if the compiled library is missing, importing a handle raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+IP_OK = 0
+IP_E_INVAL = -1
+IP_E_RANGE = -2
+IP_E_NOMEM = -3
+IP_E_CUDA = -4
+IP_E_TIMEOUT = -5
+IP_E_MAXSTEPS = -6
+IP_E_DEVICE_ASSERT = -7
+IP_E_STATE = -8
+
+PAGERANK, HASHMIN, SSSP = 0, 1, 2
+APPS = {"pagerank": PAGERANK, "hashmin": HASHMIN, "sssp": SSSP}
+PUSH_SPARSE, PUSH_DENSE, PULL = 0, 1, 2
+MODES = {"push_sparse": PUSH_SPARSE, "push_dense": PUSH_DENSE, "pull": PULL}
+POLICY_AUTO, POLICY_THRESHOLD, POLICY_MLP, POLICY_FORCED, POLICY_SEQUENCE = 0, 1, 2, 3, 4
+SELECTOR_BYTES = 16 * 4 + (32 * 8 + 32 * 32 + 3 * 32) * 2 + (32 + 32 + 3) * 4
+N_FEATURES = 8
+INF = 0xFFFFFFFF
+
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+
+
+class IPError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("damping", ctypes.c_float), ("pr_iterations", ctypes.c_uint32), ("source", ctypes.c_uint32),
+                ("policy", ctypes.c_int32), ("forced_mode", ctypes.c_int32),
+                ("mode_sequence", ctypes.POINTER(ctypes.c_uint8)), ("mode_sequence_len", ctypes.c_uint32),
+                ("t1", ctypes.c_uint32), ("t2", ctypes.c_uint32), ("thr_sparse", ctypes.c_float),
+                ("thr_pull", ctypes.c_float), ("use_graph", ctypes.c_int32), ("collect_labels", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class RunStatsC(ctypes.Structure):
+    _fields_ = [("supersteps", ctypes.c_uint32), ("halted", ctypes.c_int32), ("capacity", ctypes.c_uint32),
+                ("mode", ctypes.POINTER(ctypes.c_uint8)), ("active", _U32P), ("broadcasters", _U32P),
+                ("messages", ctypes.POINTER(ctypes.c_uint64)), ("features", ctypes.POINTER(ctypes.c_float)),
+                ("mode_ms", ctypes.POINTER(ctypes.c_float)), ("elapsed_ms", ctypes.c_float)]
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_uint32), ("n_edges", ctypes.c_uint64), ("max_out_degree", ctypes.c_uint32),
+                ("max_in_degree", ctypes.c_uint32), ("csc_is_csr", ctypes.c_uint32), ("weighted", ctypes.c_uint32),
+                ("num_sms", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+
+# every symbol include/ipregel.h declares
+EXPORTS = ("ip_options_default", "ip_graph_create", "ip_graph_destroy", "ip_graph_info", "ip_run", "ip_get_values",
+           "ip_set_selector", "ip_strerror")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the shared library (building it first if asked and it is missing/stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"{_build.LIB} is missing: run __graft_entry__.build()")
+    L = ctypes.CDLL(_build.LIB)
+    vp = ctypes.c_void_p
+    L.ip_options_default.argtypes = [ctypes.POINTER(Options)]
+    L.ip_options_default.restype = None
+    L.ip_graph_create.argtypes = [ctypes.POINTER(vp), ctypes.c_uint32, ctypes.c_uint64, vp, vp, vp, vp, vp, vp,
+                                  ctypes.c_int, vp]
+    L.ip_graph_destroy.argtypes = [vp]
+    L.ip_graph_destroy.restype = None
+    L.ip_graph_info.argtypes = [vp, ctypes.POINTER(GraphInfo)]
+    L.ip_run.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(Options), ctypes.POINTER(RunStatsC)]
+    L.ip_get_values.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int, vp]
+    L.ip_set_selector.argtypes = [vp, vp, ctypes.c_size_t]
+    L.ip_strerror.argtypes = [ctypes.c_int]
+    L.ip_strerror.restype = ctypes.c_char_p
+    for name in ("ip_graph_create", "ip_graph_info", "ip_run", "ip_get_values", "ip_set_selector"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().ip_strerror(code).decode()
+    except Exception:  # library not loadable: still describe the code
+        return {0: "ok"}.get(code, f"error {code}")
+
+
+def _check(code, where):
+    if code != IP_OK:
+        raise IPError(code, where)
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    """(pointer, is_device, keepalive) for a numpy array or torch tensor (uint32)."""
+    if a is None:
+        return None, None, None
+    if _is_torch(a):
+        import torch
+        if a.dtype not in (torch.int32, torch.uint32) and str(a.dtype) != "torch.uint32":
+            raise TypeError("uint32/int32 tensor expected")
+        if not a.is_contiguous():
+            raise ValueError("contiguous tensor expected")
+        return a.data_ptr(), a.is_cuda, a
+    arr = np.ascontiguousarray(a, dtype=np.uint32)
+    return arr.ctypes.data, False, arr
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().ip_options_default(ctypes.byref(o))
+    seq = kw.pop("mode_sequence", None)
+    for k, v in kw.items():
+        if k == "policy" and isinstance(v, str):
+            v = {"auto": POLICY_AUTO, "threshold": POLICY_THRESHOLD, "mlp": POLICY_MLP, "forced": POLICY_FORCED,
+                 "sequence": POLICY_SEQUENCE}[v]
+        if k == "forced_mode" and isinstance(v, str):
+            v = MODES[v]
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = v.cuda_stream  # torch.cuda.Stream
+        setattr(o, k, v)
+    if seq is not None:
+        buf = (ctypes.c_uint8 * len(seq))(*[MODES[m] if isinstance(m, str) else int(m) for m in seq])
+        o.mode_sequence = ctypes.cast(buf, ctypes.POINTER(ctypes.c_uint8))
+        o.mode_sequence_len = len(seq)
+        o._seq_keepalive = buf
+        if "policy" not in kw:
+            o.policy = POLICY_SEQUENCE
+    return o
+
+
+@dataclass
+class RunStats:
+    code: int
+    supersteps: int
+    halted: bool
+    elapsed_ms: float
+    mode: np.ndarray
+    active: np.ndarray
+    broadcasters: np.ndarray
+    messages: np.ndarray
+    features: np.ndarray
+    mode_ms: np.ndarray
+
+
+class Graph:
+    """A graph resident on the current CUDA device (owns its device memory)."""
+
+    def __init__(self, n, csr_offsets, csr_cols, csr_weights=None, csc_offsets=None, csc_rows=None,
+                 csc_weights=None, symmetric=False, stream=None):
+        L = load()
+        self._h = ctypes.c_void_p()
+        arrays = [csr_offsets, csr_cols, csr_weights, csc_offsets, csc_rows, csc_weights]
+        ptrs = [_ptr(a) for a in arrays]
+        dev = {p[1] for p in ptrs if p[0] is not None}
+        if len(dev) > 1:
+            raise ValueError("mix of host and device arrays")
+        device_ptrs = int(dev == {True})
+        p = [x[0] for x in ptrs]
+        if symmetric:  # declare the CSC to be the CSR itself
+            p[3], p[4], p[5] = p[0], p[1], p[2]
+        m = int(len(csr_cols)) if csr_cols is not None else 0
+        self.n = int(n)
+        self.m = m
+        st = _stream_handle(stream)
+        _check(L.ip_graph_create(ctypes.byref(self._h), self.n, m, *p, device_ptrs, st), "ip_graph_create")
+        self._keep = [x[2] for x in ptrs]
+        self._keep = None  # the library copied everything
+
+    @classmethod
+    def from_inputs(cls, g, stream=None, build_csc_on_device=False):
+        """From an inputs.Graph (host numpy arrays)."""
+        if g.symmetric:
+            return cls(g.n, g.row_ptr, g.col, g.w, symmetric=True, stream=stream)
+        if build_csc_on_device:
+            return cls(g.n, g.row_ptr, g.col, g.w, stream=stream)
+        return cls(g.n, g.row_ptr, g.col, g.w, g.t_ptr, g.t_idx, g.wt, stream=stream)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().ip_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self) -> dict:
+        i = GraphInfo()
+        _check(load().ip_graph_info(self._h, ctypes.byref(i)), "ip_graph_info")
+        return {k: getattr(i, k) for k, _ in GraphInfo._fields_}
+
+    def run(self, app, max_supersteps=100000, stats_capacity=1024, raise_on_maxsteps=False, **opts) -> RunStats:
+        app = APPS[app] if isinstance(app, str) else int(app)
+        o = default_options(**opts)
+        cap = stats_capacity
+        arr = dict(mode=np.zeros(cap, np.uint8), active=np.zeros(cap, np.uint32),
+                   broadcasters=np.zeros(cap, np.uint32), messages=np.zeros(cap, np.uint64),
+                   features=np.zeros(cap * N_FEATURES, np.float32), mode_ms=np.zeros(cap * 3, np.float32))
+        s = RunStatsC()
+        s.capacity = cap
+        s.mode = arr["mode"].ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        s.active = arr["active"].ctypes.data_as(_U32P)
+        s.broadcasters = arr["broadcasters"].ctypes.data_as(_U32P)
+        s.messages = arr["messages"].ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        s.features = arr["features"].ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        s.mode_ms = arr["mode_ms"].ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        code = load().ip_run(self._h, app, int(max_supersteps), ctypes.byref(o), ctypes.byref(s))
+        if code not in (IP_OK, IP_E_MAXSTEPS) or (raise_on_maxsteps and code == IP_E_MAXSTEPS):
+            raise IPError(code, "ip_run")
+        n = min(s.supersteps, cap)
+        return RunStats(code, s.supersteps, bool(s.halted), s.elapsed_ms, arr["mode"][:n], arr["active"][:n],
+                        arr["broadcasters"][:n], arr["messages"][:n], arr["features"].reshape(cap, N_FEATURES)[:n],
+                        arr["mode_ms"].reshape(cap, 3)[:n])
+
+    def values(self, app=None, out=None, stream=None):
+        """Values of the last run: float32 ranks or uint32 labels/distances.
+
+        out: None (returns a new numpy array) or a preallocated numpy array / CUDA tensor."""
+        L = load()
+        st = _stream_handle(stream)
+        if out is None:
+            dt = np.float32 if app == "pagerank" or app == PAGERANK else np.uint32
+            out = np.empty(self.n, dt)
+        if _is_torch(out):
+            _check(L.ip_get_values(self._h, out.data_ptr(), out.numel() * out.element_size(), int(out.is_cuda), st),
+                   "ip_get_values")
+        else:
+            _check(L.ip_get_values(self._h, out.ctypes.data, out.nbytes, 0, st), "ip_get_values")
+        return out
+
+    def set_selector(self, blob: bytes):
+        b = bytes(blob)
+        _check(load().ip_set_selector(self._h, b, len(b)), "ip_set_selector")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream

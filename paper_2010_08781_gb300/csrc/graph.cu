@@ -1,0 +1,469 @@
+// Graph store: creation (validation, upload, device-side transposition),
+// degree bins, value readback, selector upload and the small ABI helpers.
+//
+// The paper keeps one global vertex array and one global adjacency array
+// shared by all threads (Section 4.2). Here the adjacency is held twice on the
+// device: CSR (out-edges, used by push) and CSC (in-edges, used by pull,
+// Section 4.3.2), with uint32 IDs and offsets. Edge arrays are padded to a
+// multiple of four entries plus four, so kernels can read any aligned 16-byte
+// block that overlaps a vertex's edge range.
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.h"
+
+namespace ipg {
+
+int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return IP_OK;
+    if (e == cudaErrorMemoryAllocation) return IP_E_NOMEM;
+    return IP_E_CUDA;
+}
+
+#define CK(x)                              \
+    do {                                   \
+        int _r = cuda_err(x);              \
+        if (_r != IP_OK) return _r;        \
+    } while (0)
+
+int alloc_dev(ip_graph* g, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        (void)cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? IP_E_NOMEM : IP_E_CUDA;
+    }
+    g->device_bytes += bytes;
+    return IP_OK;
+}
+
+static size_t edge_alloc_count(uint64_t E) { return (size_t)(((E + 3) & ~3ull) + 4); }
+
+// ------------------------------------------------------------------ kernels
+__global__ void k_validate_offsets(const uint32_t* off, uint32_t n, uint64_t E, unsigned int* err) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (off[i + 1] < off[i]) atomicOr(err, 1u);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (off[0] != 0 || (uint64_t)off[n] != E) atomicOr(err, 1u);
+    }
+}
+
+__global__ void k_validate_ids(const uint32_t* ids, uint64_t E, uint32_t n, unsigned int* err) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E; i += (uint64_t)gridDim.x * blockDim.x)
+        if (ids[i] >= n) atomicOr(err, 2u);
+}
+
+__global__ void k_degrees(const uint32_t* off, uint32_t n, float* inv_outdeg, unsigned int* max_deg) {
+    unsigned int mx = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        uint32_t d = off[v + 1] - off[v];
+        if (inv_outdeg) inv_outdeg[v] = d ? 1.0f / (float)d : 0.0f;
+        mx = max(mx, d);
+    }
+    mx = __reduce_max_sync(FULL, mx);
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(max_deg, mx);
+}
+
+__global__ void k_count_in(const uint32_t* col, uint64_t E, uint32_t* cnt) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E; i += (uint64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[col[i]], 1u);
+}
+
+// Exclusive scan of n uint32 values in place, one CTA of 1024 threads per
+// chunk of 4096; per-chunk totals written to sums.
+__global__ void k_scan_chunks(uint32_t* data, uint64_t n, uint32_t* sums) {
+    __shared__ uint32_t warp_tot[32];
+    const uint64_t base = (uint64_t)blockIdx.x * 4096 + threadIdx.x * 4;
+    uint32_t x[4];
+    uint32_t t = 0;
+    for (int j = 0; j < 4; ++j) {
+        x[j] = base + j < n ? data[base + j] : 0u;
+        t += x[j];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = warp_tot[lane];
+        uint32_t wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
+        if (lane == 31 && sums) sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[wid] + inc - t;
+    for (int j = 0; j < 4; ++j) {
+        if (base + j < n) data[base + j] = run;
+        run += x[j];
+    }
+}
+
+__global__ void k_add_chunk_offsets(uint32_t* data, uint64_t n, const uint32_t* offs) {
+    const uint64_t base = (uint64_t)blockIdx.x * 4096;
+    const uint32_t add = offs[blockIdx.x];
+    for (uint32_t j = threadIdx.x; j < 4096; j += blockDim.x)
+        if (base + j < n) data[base + j] += add;
+}
+
+static int exclusive_scan(ip_graph* g, uint32_t* data, uint64_t n, cudaStream_t st) {
+    uint64_t chunks = (n + 4095) / 4096;
+    if (chunks <= 1) {
+        k_scan_chunks<<<1, 1024, 0, st>>>(data, n, nullptr);
+        return cuda_err(cudaGetLastError());
+    }
+    uint32_t* sums = nullptr;
+    int r = alloc_dev(g, (void**)&sums, chunks * sizeof(uint32_t));
+    if (r) return r;
+    g->device_bytes -= chunks * sizeof(uint32_t);
+    k_scan_chunks<<<(unsigned)chunks, 1024, 0, st>>>(data, n, sums);
+    r = cuda_err(cudaGetLastError());
+    if (!r) r = exclusive_scan(g, sums, chunks, st);
+    if (!r) {
+        k_add_chunk_offsets<<<(unsigned)chunks, 1024, 0, st>>>(data, n, sums);
+        r = cuda_err(cudaGetLastError());
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(sums);
+    return r;
+}
+
+// Transposition scatter: edge e = (u, v) goes to a free slot of v's in-list.
+// Slot order inside an in-list follows atomic arrival order.
+__global__ void k_scatter_in(const uint32_t* csr_off, const uint32_t* col, const uint32_t* w, uint32_t n, uint64_t E,
+                             uint32_t* cursor, uint32_t* row, uint32_t* wt) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E; e += (uint64_t)gridDim.x * blockDim.x) {
+        // source u: the last u with csr_off[u] <= e
+        uint32_t lo = 0, hi = n;  // invariant: csr_off[lo] <= e < csr_off[hi]
+        while (hi - lo > 1) {
+            uint32_t mid = lo + (hi - lo) / 2;
+            if ((uint64_t)csr_off[mid] <= e)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        uint32_t v = col[e];
+        uint32_t pos = atomicAdd(&cursor[v], 1u);
+        row[pos] = lo;
+        if (w) wt[pos] = w[e];
+    }
+}
+
+__global__ void k_heavy_list(const uint32_t* off, uint32_t n, uint32_t t2, uint32_t* list, unsigned int* count) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (off[v + 1] - off[v] >= t2) list[atomicAdd(count, 1u)] = v;
+    }
+}
+
+// ------------------------------------------------------------------ helpers
+static int grid_for(ip_graph* g, uint64_t work) {
+    uint64_t b = (work + 255) / 256;
+    uint64_t cap = (uint64_t)g->num_sms * 16;
+    if (b > cap) b = cap;
+    return (int)(b ? b : 1);
+}
+
+int ensure_bins(ip_graph* g, uint32_t t2, cudaStream_t st) {
+    if (g->bins_t2 == t2) return IP_OK;
+    unsigned int* cnt = &g->ctl->err;  // borrow: reset below
+    unsigned int zero[2] = {0, 0};
+    unsigned int h[2];
+    uint32_t* lists[2] = {g->heavy_out, g->heavy_in};
+    const uint32_t* offs[2] = {g->csr_off, g->csc_off};
+    for (int k = 0; k < 2; ++k) {
+        CK(cudaMemcpyAsync(cnt, zero, sizeof(unsigned int), cudaMemcpyHostToDevice, st));
+        k_heavy_list<<<grid_for(g, g->V), 256, 0, st>>>(offs[k], g->V, t2, lists[k], cnt);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&h[k], cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    CK(cudaMemcpyAsync(cnt, zero, sizeof(unsigned int), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    g->n_heavy_out = h[0];
+    g->n_heavy_in = h[1];
+    g->bins_t2 = t2;
+    return IP_OK;
+}
+
+static int validate_host(uint32_t n, uint64_t E, const uint32_t* off, const uint32_t* ids) {
+    if (off[0] != 0 || (uint64_t)off[n] != E) return IP_E_INVAL;
+    for (uint32_t v = 0; v < n; ++v)
+        if (off[v + 1] < off[v]) return IP_E_INVAL;
+    for (uint64_t i = 0; i < E; ++i)
+        if (ids[i] >= n) return IP_E_RANGE;
+    return IP_OK;
+}
+
+static int validate_device(ip_graph* g, const uint32_t* off, const uint32_t* ids, cudaStream_t st) {
+    unsigned int* err = &g->ctl->err;
+    CK(cudaMemsetAsync(err, 0, sizeof(unsigned int), st));
+    k_validate_offsets<<<grid_for(g, g->V), 256, 0, st>>>(off, g->V, g->E, err);
+    CK(cudaGetLastError());
+    k_validate_ids<<<grid_for(g, g->E), 256, 0, st>>>(ids, g->E, g->V, err);
+    CK(cudaGetLastError());
+    unsigned int h = 0;
+    CK(cudaMemcpyAsync(&h, err, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemsetAsync(err, 0, sizeof(unsigned int), st));
+    if (h & 1u) return IP_E_INVAL;
+    if (h & 2u) return IP_E_RANGE;
+    return IP_OK;
+}
+
+static int upload(ip_graph* g, uint32_t** dst, const uint32_t* src, size_t count, size_t alloc_count, int device_ptrs,
+                  cudaStream_t st) {
+    int r = alloc_dev(g, (void**)dst, alloc_count * sizeof(uint32_t));
+    if (r) return r;
+    if (alloc_count > count) CK(cudaMemsetAsync(*dst + count, 0, (alloc_count - count) * sizeof(uint32_t), st));
+    if (count)
+        CK(cudaMemcpyAsync(*dst, src, count * sizeof(uint32_t),
+                           device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    return IP_OK;
+}
+
+static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, const uint32_t* csr_col,
+                  const uint32_t* csr_w, const uint32_t* csc_off, const uint32_t* csc_row, const uint32_t* csc_w,
+                  int device_ptrs, cudaStream_t st) {
+    CK(cudaGetDevice(&g->device));
+    CK(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+    g->V = n;
+    g->E = E;
+    g->W = ((n + 31) / 32 + 31) & ~31u;
+    g->weighted = csr_w != nullptr;
+    int r;
+    // control block first: validation uses its error word
+    if ((r = alloc_dev(g, (void**)&g->ctl, sizeof(DevCtl)))) return r;
+    CK(cudaMemsetAsync(g->ctl, 0, sizeof(DevCtl), st));
+    CK(cudaMallocHost((void**)&g->ctl_host, sizeof(DevCtl)));
+
+    const bool alias = csc_off != nullptr && csc_off == csr_off && csc_row == csr_col;
+    if (!device_ptrs) {
+        if ((r = validate_host(n, E, csr_off, csr_col))) return r;
+        if (csc_off && !alias && (r = validate_host(n, E, csc_off, csc_row))) return r;
+    }
+    const size_t ea = edge_alloc_count(E);
+    if ((r = upload(g, &g->csr_off, csr_off, (size_t)n + 1, (size_t)n + 1, device_ptrs, st))) return r;
+    if ((r = upload(g, &g->csr_col, csr_col, E, ea, device_ptrs, st))) return r;
+    if (csr_w && (r = upload(g, &g->csr_w, csr_w, E, ea, device_ptrs, st))) return r;
+    if (device_ptrs) {
+        if ((r = validate_device(g, g->csr_off, g->csr_col, st))) return r;
+    }
+    if (alias) {
+        g->csc_alias = true;
+        g->csc_off = g->csr_off;
+        g->csc_row = g->csr_col;
+        g->csc_w = g->csr_w;
+    } else if (csc_off) {
+        if ((r = upload(g, &g->csc_off, csc_off, (size_t)n + 1, (size_t)n + 1, device_ptrs, st))) return r;
+        if ((r = upload(g, &g->csc_row, csc_row, E, ea, device_ptrs, st))) return r;
+        if (csc_w && (r = upload(g, &g->csc_w, csc_w, E, ea, device_ptrs, st))) return r;
+        if (device_ptrs && (r = validate_device(g, g->csc_off, g->csc_row, st))) return r;
+    } else {
+        // transpose on the device: count, scan, scatter
+        if ((r = alloc_dev(g, (void**)&g->csc_off, ((size_t)n + 1) * sizeof(uint32_t)))) return r;
+        if ((r = alloc_dev(g, (void**)&g->csc_row, ea * sizeof(uint32_t)))) return r;
+        CK(cudaMemsetAsync(g->csc_row, 0, ea * sizeof(uint32_t), st));
+        if (csr_w) {
+            if ((r = alloc_dev(g, (void**)&g->csc_w, ea * sizeof(uint32_t)))) return r;
+            CK(cudaMemsetAsync(g->csc_w, 0, ea * sizeof(uint32_t), st));
+        }
+        CK(cudaMemsetAsync(g->csc_off, 0, ((size_t)n + 1) * sizeof(uint32_t), st));
+        if (E) {
+            k_count_in<<<grid_for(g, E), 256, 0, st>>>(g->csr_col, E, g->csc_off);
+            CK(cudaGetLastError());
+        }
+        if ((r = exclusive_scan(g, g->csc_off, (uint64_t)n + 1, st))) return r;
+        uint32_t* cursor = nullptr;
+        if ((r = alloc_dev(g, (void**)&cursor, (size_t)n * sizeof(uint32_t)))) return r;
+        g->device_bytes -= (size_t)n * sizeof(uint32_t);
+        CK(cudaMemcpyAsync(cursor, g->csc_off, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        if (E) {
+            k_scatter_in<<<grid_for(g, E), 256, 0, st>>>(g->csr_off, g->csr_col, g->csr_w, n, E, cursor, g->csc_row,
+                                                          g->csc_w);
+        }
+        cudaError_t e1 = cudaGetLastError();
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        cudaFree(cursor);
+        CK(e1);
+        CK(e2);
+    }
+    if (csr_w && !g->csc_w) return IP_E_INVAL;
+
+    // per-vertex arrays
+    const size_t nv = (size_t)n;
+    if ((r = alloc_dev(g, (void**)&g->inv_outdeg, nv * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->value, nv * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->rank, nv * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->contrib[0], nv * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->contrib[1], nv * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->mbox, nv * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->mboxf, nv * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->recv, (size_t)g->W * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->bcast, (size_t)g->W * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->rq, nv * 4))) return r;
+    for (int k = 0; k < 2; ++k) {
+        if ((r = alloc_dev(g, (void**)&g->bq[k], nv * 4))) return r;
+        if ((r = alloc_dev(g, (void**)&g->hq[k], nv * 4))) return r;
+    }
+    if ((r = alloc_dev(g, (void**)&g->heavy_out, nv * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->heavy_in, nv * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->sel, sizeof(SelectorDev)))) return r;
+    CK(cudaMemsetAsync(g->recv, 0, (size_t)g->W * 4, st));
+    CK(cudaMemsetAsync(g->bcast, 0, (size_t)g->W * 4, st));
+
+    unsigned int* mx = &g->ctl->err;
+    CK(cudaMemsetAsync(mx, 0, 4, st));
+    k_degrees<<<grid_for(g, n), 256, 0, st>>>(g->csr_off, n, g->inv_outdeg, mx);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&g->max_out_deg, mx, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemsetAsync(mx, 0, 4, st));
+    k_degrees<<<grid_for(g, n), 256, 0, st>>>(g->csc_off, n, nullptr, mx);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&g->max_in_deg, mx, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemsetAsync(mx, 0, 4, st));
+    g->bins_t2 = 0;
+    if ((r = ensure_bins(g, DEFAULT_T2, st))) return r;
+    CK(cudaEventCreate(&g->ev0));
+    CK(cudaEventCreate(&g->ev1));
+    CK(cudaStreamSynchronize(st));
+    return IP_OK;
+}
+
+}  // namespace ipg
+
+using namespace ipg;
+
+extern "C" {
+
+void ip_options_default(ip_options_t* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->damping = 0.85f;
+    o->pr_iterations = 30;
+    o->source = 0;
+    o->policy = IP_POLICY_AUTO;
+    o->forced_mode = IP_MODE_PULL;
+    o->t1 = 0;
+    o->t2 = 0;
+    o->thr_sparse = 0.02f;
+    o->thr_pull = 0.15f;
+    o->use_graph = 1;
+    o->collect_labels = 0;
+    o->stream = nullptr;
+}
+
+void ip_graph_destroy(ip_graph_t* g) {
+    if (!g) return;
+    free_graph_exec(g);
+    void* bufs[] = {g->ctl, g->csr_off, g->csr_col, g->csr_w, g->inv_outdeg, g->value, g->rank, g->contrib[0],
+                    g->contrib[1], g->mbox, g->mboxf, g->recv, g->bcast, g->rq, g->bq[0], g->bq[1], g->hq[0],
+                    g->hq[1], g->heavy_out, g->heavy_in, g->log, g->sel, g->snap_value, g->snap_bcast};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    if (!g->csc_alias) {
+        if (g->csc_off) cudaFree(g->csc_off);
+        if (g->csc_row) cudaFree(g->csc_row);
+        if (g->csc_w) cudaFree(g->csc_w);
+    }
+    if (g->ctl_host) cudaFreeHost(g->ctl_host);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    delete g;
+}
+
+int ip_graph_create(ip_graph_t** out, uint32_t n_vertices, uint64_t n_edges, const uint32_t* csr_offsets,
+                    const uint32_t* csr_cols, const uint32_t* csr_weights, const uint32_t* csc_offsets,
+                    const uint32_t* csc_rows, const uint32_t* csc_weights, int device_ptrs, void* stream) {
+    if (!out) return IP_E_INVAL;
+    *out = nullptr;
+    if (n_vertices == 0 || n_vertices == 0xFFFFFFFFu || !csr_offsets) return IP_E_INVAL;
+    if (n_edges >= 0xFFFFFFFFull) return IP_E_RANGE;
+    if (n_edges > 0 && !csr_cols) return IP_E_INVAL;
+    if ((csc_offsets == nullptr) != (csc_rows == nullptr) && n_edges > 0) return IP_E_INVAL;
+    const bool alias = csc_offsets && csc_offsets == csr_offsets && csc_rows == csr_cols;
+    if (alias && csc_weights && csc_weights != csr_weights) return IP_E_INVAL;
+    if (csc_offsets && !alias && csr_weights && !csc_weights) return IP_E_INVAL;
+    ip_graph* g = new (std::nothrow) ip_graph();
+    if (!g) return IP_E_NOMEM;
+    int r = create(g, n_vertices, n_edges, csr_offsets, csr_cols, csr_weights, csc_offsets, csc_rows,
+                   csr_weights ? csc_weights : nullptr, device_ptrs, (cudaStream_t)stream);
+    if (r != IP_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        (void)cudaGetLastError();
+        ip_graph_destroy(g);
+        return r;
+    }
+    *out = g;
+    return IP_OK;
+}
+
+int ip_graph_info(const ip_graph_t* g, ip_graph_info_t* info) {
+    if (!g || !info) return IP_E_INVAL;
+    info->n_vertices = g->V;
+    info->n_edges = g->E;
+    info->max_out_degree = g->max_out_deg;
+    info->max_in_degree = g->max_in_deg;
+    info->csc_is_csr = g->csc_alias ? 1u : 0u;
+    info->weighted = g->weighted ? 1u : 0u;
+    info->num_sms = (uint32_t)g->num_sms;
+    info->device_bytes = g->device_bytes;
+    return IP_OK;
+}
+
+int ip_get_values(ip_graph_t* g, void* dst, size_t dst_bytes, int dst_is_device, void* stream) {
+    if (!g || !dst) return IP_E_INVAL;
+    if (g->last_app < 0) return IP_E_STATE;
+    const size_t need = (size_t)g->V * 4;
+    if (dst_bytes < need) return IP_E_RANGE;
+    const void* src = g->last_app == IP_PAGERANK ? (const void*)g->rank : (const void*)g->value;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(dst, src, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return IP_OK;
+}
+
+int ip_set_selector(ip_graph_t* g, const void* blob, size_t bytes) {
+    if (!g || !blob) return IP_E_INVAL;
+    if (bytes != IP_SELECTOR_BYTES) return IP_E_RANGE;
+    CK(cudaMemcpy(g->sel, blob, bytes, cudaMemcpyHostToDevice));
+    g->has_selector = true;
+    free_graph_exec(g);
+    return IP_OK;
+}
+
+int ip_run(ip_graph_t* g, ip_app_t app, uint32_t max_supersteps, const ip_options_t* opt, ip_run_stats_t* stats) {
+    if (!g) return IP_E_INVAL;
+    if (app != IP_PAGERANK && app != IP_HASHMIN && app != IP_SSSP) return IP_E_INVAL;
+    if (max_supersteps == 0) return IP_E_INVAL;
+    return run_app(g, (int)app, max_supersteps, opt, stats);
+}
+
+const char* ip_strerror(int code) {
+    switch (code) {
+        case IP_OK: return "ok";
+        case IP_E_INVAL: return "invalid argument or malformed graph";
+        case IP_E_RANGE: return "value out of range";
+        case IP_E_NOMEM: return "device allocation failed";
+        case IP_E_CUDA: return "CUDA runtime error";
+        case IP_E_TIMEOUT: return "bounded device wait timed out";
+        case IP_E_MAXSTEPS: return "superstep cap reached before global halt";
+        case IP_E_DEVICE_ASSERT: return "device-side check failed";
+        case IP_E_STATE: return "call not valid in the current state";
+        default: return "unknown error code";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ipregel.h"
+
+namespace ipg {
+
+constexpr uint32_t INF = 0xFFFFFFFFu;
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr int APP_PR = IP_PAGERANK, APP_HM = IP_HASHMIN, APP_SSSP = IP_SSSP;
+constexpr int N_FEATURES = 8;
+constexpr uint32_t MAX_SEQ = 64;
+constexpr int BLOCK = 256;  // threads per CTA for every superstep kernel
+constexpr uint32_t DEFAULT_T1 = 32;
+constexpr uint32_t DEFAULT_T2 = 4096;
+
+// Device control block: the counters the kernels of one superstep fill, and the
+// decision the selector kernel takes after it. Lives in device memory; the host
+// reads it back only in the host-driven loop.
+struct DevCtl {
+    // statistics of the superstep being completed (filled by init / apply kernels)
+    unsigned int n_active;  // vertices that ran compute()
+    unsigned int n_bcast;   // vertices that broadcast
+    unsigned long long msgs;  // messages sent = sum of out-degrees of broadcasters
+    unsigned int max_deg;   // largest out-degree among broadcasters
+    unsigned int rq_len;    // recipient queue length (push-sparse)
+    unsigned int bq_len[2]; // light broadcaster queue lengths, by superstep parity
+    unsigned int hq_len[2]; // heavy broadcaster queue lengths, by superstep parity
+    unsigned int q_valid;   // queue of parity (superstep & 1) holds exactly the bcast bitmap
+    // decision state (owned by the selector kernel)
+    unsigned int superstep; // superstep being computed; at selector time, the one just completed
+    unsigned int mode;      // mode of the next exchange
+    unsigned int mode_used; // mode of the exchange that delivered into `superstep`
+    unsigned int done;      // 0 running, 1 halted, 2 superstep cap reached
+    unsigned int err;       // device-side error bits
+    unsigned int prev_bcast;
+    unsigned int pad0;
+    unsigned long long t_prev;  // %globaltimer at the previous selector call
+};
+
+// One record per superstep, written by the selector kernel.
+struct LogRec {
+    unsigned int mode;
+    unsigned int active;
+    unsigned int bcast;
+    unsigned int max_deg;
+    unsigned long long msgs;
+    float feat[N_FEATURES];
+};
+
+// Learned selector parameters on the device (layout of IP_SELECTOR_BYTES).
+struct SelectorDev {
+    float mu[8], sd[8];
+    uint16_t W1[32 * 8], W2[32 * 32], W3[3 * 32];
+    float b1[32], b2[32], b3[3];
+};
+static_assert(sizeof(SelectorDev) == IP_SELECTOR_BYTES, "selector layout");
+
+// Everything a superstep kernel needs, passed by value.
+struct Params {
+    uint32_t V;
+    uint32_t W;      // bitmap words, padded to a multiple of 32
+    uint64_t E;
+    const uint32_t* csr_off;
+    const uint32_t* csr_col;
+    const uint32_t* csr_w;
+    const uint32_t* csc_off;
+    const uint32_t* csc_row;
+    const uint32_t* csc_w;
+    const uint32_t* heavy_out;  // vertices with out-degree >= t2
+    const uint32_t* heavy_in;   // vertices with in-degree >= t2
+    uint32_t n_heavy_out, n_heavy_in;
+    const float* inv_outdeg;
+    uint32_t* value;
+    float* rank;
+    float* contrib0;
+    float* contrib1;
+    uint32_t* mbox;
+    float* mboxf;
+    uint32_t* recv;
+    uint32_t* bcast;
+    uint32_t* rq;
+    uint32_t* bq0;
+    uint32_t* bq1;
+    uint32_t* hq0;
+    uint32_t* hq1;
+    DevCtl* ctl;
+    LogRec* log;
+    uint32_t log_cap;
+    const SelectorDev* sel;
+    uint32_t t1, t2;
+    float thr_sparse, thr_pull;
+    uint32_t app, T, source, max_supersteps;
+    float damping, pr_base;  // pr_base = (1-d)/N rounded to float
+    int32_t policy, forced_mode;
+    uint32_t seq_len;
+    uint8_t seq[MAX_SEQ];
+    uint32_t max_out_deg;
+    uint32_t out_deg_src;
+    int32_t use_graph;
+    cudaGraphConditionalHandle h_while, h_switch;
+};
+
+}  // namespace ipg
+
+struct ip_graph {
+    int device = 0;
+    int num_sms = 0;
+    uint32_t V = 0;
+    uint64_t E = 0;
+    uint32_t W = 0;
+    uint32_t* csr_off = nullptr;
+    uint32_t* csr_col = nullptr;
+    uint32_t* csr_w = nullptr;
+    uint32_t* csc_off = nullptr;
+    uint32_t* csc_row = nullptr;
+    uint32_t* csc_w = nullptr;
+    bool csc_alias = false;
+    bool weighted = false;
+    uint32_t max_out_deg = 0, max_in_deg = 0;
+    float* inv_outdeg = nullptr;
+    uint32_t bins_t2 = 0;
+    uint32_t* heavy_out = nullptr;
+    uint32_t* heavy_in = nullptr;
+    uint32_t n_heavy_out = 0, n_heavy_in = 0;
+    // run state
+    uint32_t* value = nullptr;
+    float* rank = nullptr;
+    float* contrib[2] = {nullptr, nullptr};
+    uint32_t* mbox = nullptr;
+    float* mboxf = nullptr;
+    uint32_t* recv = nullptr;
+    uint32_t* bcast = nullptr;
+    uint32_t* rq = nullptr;
+    uint32_t* bq[2] = {nullptr, nullptr};
+    uint32_t* hq[2] = {nullptr, nullptr};
+    ipg::DevCtl* ctl = nullptr;
+    ipg::DevCtl* ctl_host = nullptr;  // pinned mirror
+    ipg::LogRec* log = nullptr;
+    uint32_t log_cap = 0;
+    ipg::SelectorDev* sel = nullptr;
+    bool has_selector = false;
+    int last_app = -1;
+    uint64_t device_bytes = 0;
+    // scratch used by label collection (snapshots)
+    uint32_t* snap_value = nullptr;
+    uint32_t* snap_bcast = nullptr;
+    // cached CUDA graph of the last device-side run
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    unsigned char gkey[sizeof(ipg::Params)] = {0};
+    bool has_gkey = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int grid[16] = {0};
+    bool grids_ready = false;
+};
+
+namespace ipg {
+// graph.cu
+int alloc_dev(ip_graph* g, void** p, size_t bytes);
+int ensure_bins(ip_graph* g, uint32_t t2, cudaStream_t st);
+int cuda_err(cudaError_t e);
+// superstep.cu
+int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* opt, ip_run_stats_t* stats);
+void free_graph_exec(ip_graph* g);
+}  // namespace ipg

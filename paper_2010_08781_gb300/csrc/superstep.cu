@@ -1,0 +1,1163 @@
+// Synchronous vertex-centric supersteps on sm_103a.
+//
+// One superstep s >= 1 (Section 4.2, Fig. 3) is:
+//   exchange  deliver the messages broadcast in superstep s-1 into the one-slot
+//             mailboxes (Section 4.3.3), in one of three modes (Section 4.3.2):
+//               push-sparse  senders taken from a compacted queue (selection
+//                            bypass, Section 4.3.1); the first message to reach
+//                            a vertex appends it to the recipient queue
+//               push-dense   senders taken from the broadcast bitmap
+//               pull         every vertex folds its in-neighbours' broadcasts
+//             Push combines with atomicMin (min apps) or atomicAdd (PageRank):
+//             the lock-free combiners that Section 4.3.2 leaves as future work.
+//   apply     compute() of every recipient (Figs. 9, 10) or of every vertex
+//             (PageRank, Fig. 8): read and reset the mailbox, update the value,
+//             decide whether to broadcast, vote to halt; also the frontier
+//             statistics of the superstep.
+//   select    one warp: halt test (Section 4.2: every vertex halted and no
+//             message in flight), frontier features, mode of the next exchange
+//             (threshold rule or the learned MLP), per-superstep log.
+// PageRank's pull mode fuses exchange and apply: the broadcast value is held in
+// two buffers (read s-1, write s), so one kernel per superstep suffices.
+//
+// Scheduling (degree bins): a vertex with degree <= t1 is handled by one lane,
+// t1 < degree < t2 by a whole warp, degree >= t2 by a whole CTA. Edge arrays are
+// read as aligned 16-byte blocks.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace ipg {
+
+// ----------------------------------------------------------------- helpers
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
+    uint32_t s = a + b;
+    return s < a ? INF : s;
+}
+__device__ __forceinline__ uint4 ld4(const uint32_t* p, uint32_t blk) {
+    return __ldg(reinterpret_cast<const uint4*>(p) + blk);
+}
+__device__ __forceinline__ uint32_t qa(const uint4& q, int j) {
+    return j == 0 ? q.x : (j == 1 ? q.y : (j == 2 ? q.z : q.w));
+}
+__device__ __forceinline__ bool bit_of(const uint32_t* bm, uint32_t v) {
+    return (__ldg(bm + (v >> 5)) >> (v & 31u)) & 1u;
+}
+__device__ __forceinline__ uint32_t global_warp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ uint32_t num_warps() { return (gridDim.x * blockDim.x) >> 5; }
+
+// All 32 lanes call; lanes with pred append v to q (one atomic per warp).
+__device__ __forceinline__ void warp_append(bool pred, uint32_t v, uint32_t* q, unsigned int* len) {
+    const uint32_t m = __ballot_sync(FULL, pred);
+    if (!m) return;
+    const uint32_t leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane_id() == leader) base = atomicAdd(len, (unsigned int)__popc(m));
+    base = __shfl_sync(FULL, base, leader);
+    if (pred) q[base + __popc(m & lanemask_lt())] = v;
+}
+
+// Error-free transformation of a + b (Knuth's TwoSum): s + err == a + b exactly.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (x - bp);
+    s = t;
+    c += err;
+}
+
+struct Stats {
+    unsigned int act, bc, maxd;
+    unsigned long long msgs;
+};
+
+// Block-wide reduction of the superstep statistics, one atomic per field per CTA.
+__device__ void flush_stats(Stats st, DevCtl* ctl) {
+    __shared__ Stats sh[BLOCK / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        st.act += __shfl_down_sync(FULL, st.act, o);
+        st.bc += __shfl_down_sync(FULL, st.bc, o);
+        st.msgs += __shfl_down_sync(FULL, st.msgs, o);
+        st.maxd = max(st.maxd, __shfl_down_sync(FULL, st.maxd, o));
+    }
+    const int w = threadIdx.x >> 5;
+    if (lane_id() == 0) sh[w] = st;
+    __syncthreads();
+    if (w == 0) {
+        Stats t = lane_id() < blockDim.x / 32 ? sh[lane_id()] : Stats{0, 0, 0, 0};
+        for (int o = 16; o > 0; o >>= 1) {
+            t.act += __shfl_down_sync(FULL, t.act, o);
+            t.bc += __shfl_down_sync(FULL, t.bc, o);
+            t.msgs += __shfl_down_sync(FULL, t.msgs, o);
+            t.maxd = max(t.maxd, __shfl_down_sync(FULL, t.maxd, o));
+        }
+        if (lane_id() == 0) {
+            if (t.act) atomicAdd(&ctl->n_active, t.act);
+            if (t.bc) atomicAdd(&ctl->n_bcast, t.bc);
+            if (t.msgs) atomicAdd(&ctl->msgs, t.msgs);
+            if (t.maxd) atomicMax(&ctl->max_deg, t.maxd);
+        }
+    }
+}
+
+// =========================================================== superstep 0
+// Hashmin (Fig. 9): value = id, everybody broadcasts. SSSP (Fig. 10): the
+// source takes 0 and broadcasts, everybody else INF.
+__global__ void k_init_min(Params P) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const bool hm = P.app == APP_HM;
+    for (uint32_t v = tid; v < P.V; v += nth) {
+        P.value[v] = hm ? v : (v == P.source ? 0u : INF);
+        P.mbox[v] = INF;
+    }
+    for (uint32_t w = tid; w < P.W; w += nth) {
+        P.recv[w] = 0;
+        uint32_t b = 0;
+        if (hm) {
+            const uint64_t lo = (uint64_t)w * 32;
+            if (lo + 32 <= P.V)
+                b = FULL;
+            else if (lo < P.V)
+                b = (1u << (P.V - lo)) - 1u;
+        } else if (w == (P.source >> 5)) {
+            b = 1u << (P.source & 31u);
+        }
+        P.bcast[w] = b;
+    }
+    if (tid == 0) {
+        DevCtl* c = P.ctl;
+        c->superstep = 0;
+        c->mode_used = 255;
+        c->done = 0;
+        c->err = 0;
+        c->prev_bcast = 0;
+        c->t_prev = globaltimer();
+        c->n_active = P.V;
+        c->rq_len = 0;
+        c->bq_len[0] = c->bq_len[1] = 0;
+        c->hq_len[0] = c->hq_len[1] = 0;
+        if (hm) {
+            c->n_bcast = P.V;
+            c->msgs = P.E;
+            c->max_deg = P.max_out_deg;
+            c->q_valid = 0;
+        } else {
+            c->n_bcast = 1;
+            c->msgs = P.out_deg_src;
+            c->max_deg = P.out_deg_src;
+            if (P.out_deg_src >= P.t2) {
+                P.hq0[0] = P.source;
+                c->hq_len[0] = 1;
+            } else {
+                P.bq0[0] = P.source;
+                c->bq_len[0] = 1;
+            }
+            c->q_valid = 1;
+        }
+    }
+}
+
+// PageRank superstep 0 (Fig. 8): value = 1/N, broadcast value / out-degree.
+__global__ void k_pr_init(Params P) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const float r0 = 1.0f / (float)P.V;
+    for (uint32_t v = tid; v < P.V; v += nth) {
+        P.rank[v] = r0;
+        P.contrib0[v] = P.T > 0 ? r0 * P.inv_outdeg[v] : 0.0f;
+        P.mboxf[v] = 0.0f;
+    }
+    if (tid == 0) {
+        DevCtl* c = P.ctl;
+        c->superstep = 0;
+        c->mode_used = 255;
+        c->done = 0;
+        c->err = 0;
+        c->prev_bcast = 0;
+        c->t_prev = globaltimer();
+    }
+}
+
+// ============================================================ push (min apps)
+template <int APP, bool SPARSE>
+__device__ __forceinline__ void push_edge(const Params& P, bool live, uint32_t v, uint32_t msg) {
+    bool first = false;
+    if (live) {
+        if (msg < __ldcg(P.mbox + v)) atomicMin(P.mbox + v, msg);
+        const uint32_t bit = 1u << (v & 31u);
+        uint32_t* rw = P.recv + (v >> 5);
+        if (!(__ldcg(rw) & bit)) first = !(atomicOr(rw, bit) & bit);
+    }
+    if (SPARSE) warp_append(first, v, P.rq, &P.ctl->rq_len);
+}
+
+template <int APP>
+__device__ __forceinline__ uint32_t edge_msg(uint32_t val, const uint4& qw, int j) {
+    if (APP == APP_HM) return val;
+    return sat_add(val, qa(qw, j));
+}
+
+// Edges of the 16-byte block `blk`, restricted to [beg, end), pushed with value val.
+template <int APP, bool SPARSE>
+__device__ __forceinline__ void push_block(const Params& P, bool ok, uint32_t blk, uint32_t beg, uint32_t end,
+                                           uint32_t val) {
+    uint4 qc = make_uint4(0, 0, 0, 0), qw = make_uint4(1, 1, 1, 1);
+    if (ok) {
+        qc = ld4(P.csr_col, blk);
+        if (APP == APP_SSSP && P.csr_w) qw = ld4(P.csr_w, blk);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t e = blk * 4 + j;
+        const bool live = ok && e >= beg && e < end;
+        push_edge<APP, SPARSE>(P, live, qa(qc, j), edge_msg<APP>(val, qw, j));
+    }
+}
+
+// A warp pushes the broadcasts of up to 32 lane-owned senders (degree < t2).
+template <int APP, bool SPARSE>
+__device__ __forceinline__ void push_group(const Params& P, uint32_t u, bool act) {
+    uint32_t beg = 0, end = 0, val = 0;
+    if (act) {
+        beg = P.csr_off[u];
+        end = P.csr_off[u + 1];
+        val = P.value[u];
+    }
+    const uint32_t deg = end - beg;
+    const bool small = act && deg > 0 && deg <= P.t1;
+    const bool med = act && deg > P.t1 && deg < P.t2;
+    // lane-owned senders
+    const uint32_t b0 = beg >> 2;
+    const uint32_t nb = small ? ((end + 3) >> 2) - b0 : 0;
+    const uint32_t maxnb = __reduce_max_sync(FULL, nb);
+    for (uint32_t it = 0; it < maxnb; ++it) push_block<APP, SPARSE>(P, it < nb, b0 + it, beg, end, val);
+    // warp-owned senders
+    uint32_t mm = __ballot_sync(FULL, med);
+    while (mm) {
+        const int l = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const uint32_t mb = __shfl_sync(FULL, beg, l), me = __shfl_sync(FULL, end, l);
+        const uint32_t mv = __shfl_sync(FULL, val, l);
+        const uint32_t bs = mb >> 2, be = (me + 3) >> 2;
+        const uint32_t iters = (be - bs + 31) >> 5;
+        for (uint32_t k = 0; k < iters; ++k) {
+            const uint32_t blk = bs + k * 32 + lane_id();
+            push_block<APP, SPARSE>(P, blk < be, blk, mb, me, mv);
+        }
+    }
+}
+
+// A whole CTA pushes the broadcast of one sender with degree >= t2.
+template <int APP, bool SPARSE>
+__device__ __forceinline__ void push_heavy(const Params& P, uint32_t u) {
+    const uint32_t beg = P.csr_off[u], end = P.csr_off[u + 1], val = P.value[u];
+    const uint32_t bs = beg >> 2, be = (end + 3) >> 2;
+    const uint32_t iters = (be - bs + blockDim.x - 1) / blockDim.x;
+    for (uint32_t k = 0; k < iters; ++k) {
+        const uint32_t blk = bs + k * blockDim.x + threadIdx.x;
+        push_block<APP, SPARSE>(P, blk < be, blk, beg, end, val);
+    }
+}
+
+template <int APP, bool SPARSE>
+__global__ void __launch_bounds__(BLOCK) k_push(Params P) {
+    const uint32_t s = P.ctl->superstep - 1;  // deliver the broadcasts of superstep s
+    const int par = s & 1;
+    if (SPARSE) {
+        const uint32_t nh = P.ctl->hq_len[par];
+        const uint32_t* hq = par ? P.hq1 : P.hq0;
+        for (uint32_t i = blockIdx.x; i < nh; i += gridDim.x) {
+            const uint32_t u = hq[i];
+            if (threadIdx.x == 0) P.bcast[u >> 5] = 0;  // consumed: clear the sender's bitmap word
+            push_heavy<APP, SPARSE>(P, u);
+        }
+        const uint32_t n = P.ctl->bq_len[par];
+        const uint32_t* q = par ? P.bq1 : P.bq0;
+        for (uint32_t base = global_warp() * 32; base < n; base += num_warps() * 32) {
+            const uint32_t i = base + lane_id();
+            const bool act = i < n;
+            const uint32_t u = act ? q[i] : 0;
+            if (act) P.bcast[u >> 5] = 0;
+            push_group<APP, SPARSE>(P, u, act);
+        }
+    } else {
+        for (uint32_t i = blockIdx.x; i < P.n_heavy_out; i += gridDim.x) {
+            const uint32_t u = P.heavy_out[i];
+            if (bit_of(P.bcast, u)) push_heavy<APP, SPARSE>(P, u);
+        }
+        // 32 bitmap words (1024 vertices) per warp iteration
+        for (uint32_t c = global_warp(); c * 32 < P.W; c += num_warps()) {
+            const uint32_t myw = P.bcast[c * 32 + lane_id()];
+            uint32_t nz = __ballot_sync(FULL, myw != 0);
+            while (nz) {
+                const int j = __ffs(nz) - 1;
+                nz &= nz - 1;
+                const uint32_t word = __shfl_sync(FULL, myw, j);
+                const uint32_t u = (c * 32 + j) * 32 + lane_id();
+                push_group<APP, SPARSE>(P, u, (word >> lane_id()) & 1u);  // heavy lanes skip inside
+            }
+        }
+    }
+}
+
+// Broadcast bitmap -> broadcaster queues of parity (superstep & 1), only when
+// the queues do not already hold the bitmap.
+__global__ void __launch_bounds__(BLOCK) k_compact(Params P) {
+    if (P.ctl->q_valid) return;
+    const uint32_t s = P.ctl->superstep - 1;  // queue the broadcasters of superstep s
+    const int par = s & 1;
+    uint32_t* q = par ? P.bq1 : P.bq0;
+    uint32_t* hq = par ? P.hq1 : P.hq0;
+    unsigned int* ql = &P.ctl->bq_len[par];
+    unsigned int* hl = &P.ctl->hq_len[par];
+    for (uint32_t c = global_warp(); c * 32 < P.W; c += num_warps()) {
+        const uint32_t myw = P.bcast[c * 32 + lane_id()];
+        uint32_t nz = __ballot_sync(FULL, myw != 0);
+        while (nz) {
+            const int j = __ffs(nz) - 1;
+            nz &= nz - 1;
+            const uint32_t word = __shfl_sync(FULL, myw, j);
+            const uint32_t u = (c * 32 + j) * 32 + lane_id();
+            const bool act = (word >> lane_id()) & 1u;
+            const uint32_t deg = act ? P.csr_off[u + 1] - P.csr_off[u] : 0;
+            warp_append(act && deg < P.t2, u, q, ql);
+            warp_append(act && deg >= P.t2, u, hq, hl);
+        }
+    }
+}
+
+// ============================================================ pull (min apps)
+// Folds the in-edges of 16-byte block blk (restricted to [beg,end)) into (m, any).
+template <int APP>
+__device__ __forceinline__ void pull_block(const Params& P, uint32_t blk, uint32_t beg, uint32_t end, uint32_t& m,
+                                           bool& any) {
+    const uint4 qr = ld4(P.csc_row, blk);
+    bool hit[4];
+    bool h = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t e = blk * 4 + j;
+        const uint32_t u = qa(qr, j);
+        hit[j] = e >= beg && e < end && bit_of(P.bcast, u);
+        h |= hit[j];
+    }
+    if (h) {
+        uint4 qw = make_uint4(1, 1, 1, 1);
+        if (APP == APP_SSSP && P.csc_w) qw = ld4(P.csc_w, blk);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (hit[j]) {
+                const uint32_t val = __ldg(P.value + qa(qr, j));
+                m = min(m, edge_msg<APP>(val, qw, j));
+                any = true;
+            }
+        }
+    }
+}
+
+template <int APP>
+__device__ __forceinline__ void pull_group(const Params& P, uint32_t tile) {
+    const uint32_t v = tile * 32 + lane_id();
+    const bool valid = v < P.V;
+    uint32_t beg = 0, end = 0;
+    if (valid) {
+        beg = P.csc_off[v];
+        end = P.csc_off[v + 1];
+    }
+    const uint32_t deg = end - beg;
+    const bool small = deg > 0 && deg <= P.t1;
+    const bool med = deg > P.t1 && deg < P.t2;
+    uint32_t m = INF;
+    bool any = false;
+    if (small) {
+        for (uint32_t blk = beg >> 2; blk < ((end + 3) >> 2); ++blk) pull_block<APP>(P, blk, beg, end, m, any);
+    }
+    uint32_t mm = __ballot_sync(FULL, med);
+    while (mm) {
+        const int l = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const uint32_t mb = __shfl_sync(FULL, beg, l), me = __shfl_sync(FULL, end, l);
+        uint32_t pm = INF;
+        bool pa = false;
+        for (uint32_t blk = (mb >> 2) + lane_id(); blk < ((me + 3) >> 2); blk += 32) pull_block<APP>(P, blk, mb, me, pm, pa);
+        pm = __reduce_min_sync(FULL, pm);
+        pa = __any_sync(FULL, pa);
+        if (lane_id() == (uint32_t)l) {
+            m = pm;
+            any = pa;
+        }
+    }
+    if (any) P.mbox[v] = m;
+    const uint32_t bits = __ballot_sync(FULL, any);
+    if (lane_id() == 0 && bits) atomicOr(P.recv + tile, bits);
+}
+
+template <int APP>
+__device__ __forceinline__ void pull_heavy(const Params& P, uint32_t v) {
+    __shared__ uint32_t sm[BLOCK / 32];
+    __shared__ int sa[BLOCK / 32];
+    const uint32_t beg = P.csc_off[v], end = P.csc_off[v + 1];
+    uint32_t m = INF;
+    bool any = false;
+    for (uint32_t blk = (beg >> 2) + threadIdx.x; blk < ((end + 3) >> 2); blk += blockDim.x)
+        pull_block<APP>(P, blk, beg, end, m, any);
+    m = __reduce_min_sync(FULL, m);
+    any = __any_sync(FULL, any);
+    if (lane_id() == 0) {
+        sm[threadIdx.x >> 5] = m;
+        sa[threadIdx.x >> 5] = any;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (uint32_t w = 1; w < blockDim.x / 32; ++w) {
+            m = min(m, sm[w]);
+            any = any || sa[w];
+        }
+        if (any) {
+            P.mbox[v] = m;
+            atomicOr(P.recv + (v >> 5), 1u << (v & 31u));
+        }
+    }
+    __syncthreads();
+}
+
+template <int APP>
+__global__ void __launch_bounds__(BLOCK) k_pull(Params P) {
+    for (uint32_t i = blockIdx.x; i < P.n_heavy_in; i += gridDim.x) pull_heavy<APP>(P, P.heavy_in[i]);
+    const uint32_t tiles = (P.V + 31) / 32;
+    for (uint32_t t = global_warp(); t < tiles; t += num_warps()) pull_group<APP>(P, t);
+}
+
+// ============================================================ apply (min apps)
+// compute() of Figs. 9 and 10 for one recipient: m is the combined message.
+__device__ __forceinline__ bool apply_vertex(const Params& P, uint32_t v, uint32_t& deg) {
+    const uint32_t m = P.mbox[v];
+    P.mbox[v] = INF;
+    const uint32_t val = P.value[v];
+    if (m < val) {
+        P.value[v] = m;
+        deg = P.csr_off[v + 1] - P.csr_off[v];
+        return true;  // broadcast the new value
+    }
+    deg = 0;
+    return false;
+}
+
+// Recipients found in the recv bitmap (after pull or push-dense).
+__global__ void __launch_bounds__(BLOCK) k_apply_bitmap(Params P) {
+    Stats st{0, 0, 0, 0};
+    for (uint32_t c = global_warp(); c * 32 < P.W; c += num_warps()) {
+        const uint32_t wi = c * 32 + lane_id();
+        const uint32_t rw = P.recv[wi];
+        if (rw == 0) P.bcast[wi] = 0;
+        uint32_t nz = __ballot_sync(FULL, rw != 0);
+        while (nz) {
+            const int j = __ffs(nz) - 1;
+            nz &= nz - 1;
+            const uint32_t bits = __shfl_sync(FULL, rw, j);
+            const uint32_t wj = c * 32 + j;
+            const uint32_t v = wj * 32 + lane_id();
+            uint32_t deg = 0;
+            const bool b = ((bits >> lane_id()) & 1u) && apply_vertex(P, v, deg);
+            const uint32_t bb = __ballot_sync(FULL, b);
+            if (lane_id() == 0) {
+                P.bcast[wj] = bb;
+                P.recv[wj] = 0;
+                st.act += __popc(bits);
+            }
+            st.bc += b;
+            st.msgs += deg;
+            st.maxd = max(st.maxd, deg);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->q_valid = 0;
+    flush_stats(st, P.ctl);
+}
+
+// Recipients taken from the recipient queue (after push-sparse); broadcasters
+// go to the queues of the next parity and to the (cleared) bitmap.
+__global__ void __launch_bounds__(BLOCK) k_apply_queue(Params P) {
+    Stats st{0, 0, 0, 0};
+    const uint32_t s1 = P.ctl->superstep;  // the superstep being computed
+    const int par = s1 & 1;
+    uint32_t* q = par ? P.bq1 : P.bq0;
+    uint32_t* hq = par ? P.hq1 : P.hq0;
+    unsigned int* ql = &P.ctl->bq_len[par];
+    unsigned int* hl = &P.ctl->hq_len[par];
+    const uint32_t n = P.ctl->rq_len;
+    for (uint32_t base = global_warp() * 32; base < n; base += num_warps() * 32) {
+        const uint32_t i = base + lane_id();
+        const bool valid = i < n;
+        uint32_t v = 0, deg = 0;
+        bool b = false;
+        if (valid) {
+            v = P.rq[i];
+            P.recv[v >> 5] = 0;  // every bit of this word belongs to a queued recipient
+            b = apply_vertex(P, v, deg);
+            if (b) atomicOr(P.bcast + (v >> 5), 1u << (v & 31u));
+        }
+        warp_append(b && deg < P.t2, v, q, ql);
+        warp_append(b && deg >= P.t2, v, hq, hl);
+        st.act += valid;
+        st.bc += b;
+        st.msgs += deg;
+        st.maxd = max(st.maxd, deg);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->q_valid = 1;
+    flush_stats(st, P.ctl);
+}
+
+// ================================================================ PageRank
+__device__ __forceinline__ void pr_finish(const Params& P, uint32_t v, float sum, uint32_t s, float* nxt) {
+    const float r = fmaf(P.damping, sum, P.pr_base);  // (1-d)/N + d * sum
+    P.rank[v] = r;
+    nxt[v] = s < P.T ? r * P.inv_outdeg[v] : 0.0f;  // broadcast value/out-degree while s < T
+}
+
+__device__ __forceinline__ void pr_pull_block(const uint32_t* row, const float* cur, uint32_t blk, uint32_t beg,
+                                              uint32_t end, float& s, float& c) {
+    const uint4 qr = ld4(row, blk);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t e = blk * 4 + j;
+        if (e >= beg && e < end) two_sum_acc(s, c, __ldg(cur + qa(qr, j)));
+    }
+}
+
+__device__ __forceinline__ void warp_two_sum(float& s, float& c) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_down_sync(FULL, s, o), oc = __shfl_down_sync(FULL, c, o);
+        two_sum_acc(s, c, os);
+        c += oc;
+    }
+}
+
+// Fused exchange + compute for PageRank pull: sum of in-neighbours' broadcasts.
+__global__ void __launch_bounds__(BLOCK) k_pr_pull(Params P) {
+    __shared__ float ss[BLOCK / 32], sc[BLOCK / 32];
+    const uint32_t s = P.ctl->superstep;  // the superstep being computed
+    const float* cur = (s & 1) ? P.contrib0 : P.contrib1;
+    float* nxt = (s & 1) ? P.contrib1 : P.contrib0;
+    for (uint32_t i = blockIdx.x; i < P.n_heavy_in; i += gridDim.x) {
+        const uint32_t v = P.heavy_in[i];
+        const uint32_t beg = P.csc_off[v], end = P.csc_off[v + 1];
+        float a = 0.f, c = 0.f;
+        for (uint32_t blk = (beg >> 2) + threadIdx.x; blk < ((end + 3) >> 2); blk += blockDim.x)
+            pr_pull_block(P.csc_row, cur, blk, beg, end, a, c);
+        warp_two_sum(a, c);
+        if (lane_id() == 0) {
+            ss[threadIdx.x >> 5] = a;
+            sc[threadIdx.x >> 5] = c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float ta = ss[0], tc = sc[0];
+            for (uint32_t w = 1; w < blockDim.x / 32; ++w) {
+                two_sum_acc(ta, tc, ss[w]);
+                tc += sc[w];
+            }
+            pr_finish(P, v, ta + tc, s, nxt);
+        }
+        __syncthreads();
+    }
+    const uint32_t tiles = (P.V + 31) / 32;
+    for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
+        const uint32_t v = t * 32 + lane_id();
+        const bool valid = v < P.V;
+        uint32_t beg = 0, end = 0;
+        if (valid) {
+            beg = P.csc_off[v];
+            end = P.csc_off[v + 1];
+        }
+        const uint32_t deg = end - beg;
+        const bool med = deg > P.t1 && deg < P.t2;
+        float a = 0.f, c = 0.f;
+        if (deg <= P.t1) {
+            for (uint32_t blk = beg >> 2; blk < ((end + 3) >> 2); ++blk) pr_pull_block(P.csc_row, cur, blk, beg, end, a, c);
+        }
+        uint32_t mm = __ballot_sync(FULL, med);
+        while (mm) {
+            const int l = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint32_t mb = __shfl_sync(FULL, beg, l), me = __shfl_sync(FULL, end, l);
+            float pa = 0.f, pc = 0.f;
+            for (uint32_t blk = (mb >> 2) + lane_id(); blk < ((me + 3) >> 2); blk += 32)
+                pr_pull_block(P.csc_row, cur, blk, mb, me, pa, pc);
+            warp_two_sum(pa, pc);
+            pa = __shfl_sync(FULL, pa, 0);
+            pc = __shfl_sync(FULL, pc, 0);
+            if (lane_id() == (uint32_t)l) {
+                a = pa;
+                c = pc;
+            }
+        }
+        if (valid && deg < P.t2) pr_finish(P, v, a + c, s, nxt);
+    }
+}
+
+// PageRank push: every vertex adds value/out-degree into its out-neighbours' mailboxes.
+__device__ __forceinline__ void pr_push_block(const Params& P, bool ok, uint32_t blk, uint32_t beg, uint32_t end,
+                                              float x) {
+    if (!ok) return;
+    const uint4 qc = ld4(P.csr_col, blk);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t e = blk * 4 + j;
+        if (e >= beg && e < end) atomicAdd(P.mboxf + qa(qc, j), x);
+    }
+}
+
+__global__ void __launch_bounds__(BLOCK) k_pr_push(Params P) {
+    const uint32_t s = P.ctl->superstep - 1;  // deliver the broadcasts of superstep s
+    const float* cur = (s & 1) ? P.contrib1 : P.contrib0;
+    for (uint32_t i = blockIdx.x; i < P.n_heavy_out; i += gridDim.x) {
+        const uint32_t u = P.heavy_out[i];
+        const uint32_t beg = P.csr_off[u], end = P.csr_off[u + 1];
+        const float x = cur[u];
+        for (uint32_t blk = (beg >> 2) + threadIdx.x; blk < ((end + 3) >> 2); blk += blockDim.x)
+            pr_push_block(P, true, blk, beg, end, x);
+    }
+    const uint32_t tiles = (P.V + 31) / 32;
+    for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
+        const uint32_t u = t * 32 + lane_id();
+        const bool valid = u < P.V;
+        uint32_t beg = 0, end = 0;
+        float x = 0.f;
+        if (valid) {
+            beg = P.csr_off[u];
+            end = P.csr_off[u + 1];
+            x = cur[u];
+        }
+        const uint32_t deg = end - beg;
+        if (deg <= P.t1) {
+            for (uint32_t blk = beg >> 2; blk < ((end + 3) >> 2); ++blk) pr_push_block(P, true, blk, beg, end, x);
+        }
+        uint32_t mm = __ballot_sync(FULL, deg > P.t1 && deg < P.t2);
+        while (mm) {
+            const int l = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint32_t mb = __shfl_sync(FULL, beg, l), me = __shfl_sync(FULL, end, l);
+            const float mx = __shfl_sync(FULL, x, l);
+            for (uint32_t blk = (mb >> 2) + lane_id(); blk < ((me + 3) >> 2); blk += 32)
+                pr_push_block(P, true, blk, mb, me, mx);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BLOCK) k_pr_apply(Params P) {
+    const uint32_t s = P.ctl->superstep;  // the superstep being computed
+    float* nxt = (s & 1) ? P.contrib1 : P.contrib0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < P.V; v += gridDim.x * blockDim.x) {
+        const float sum = P.mboxf[v];
+        P.mboxf[v] = 0.0f;
+        pr_finish(P, v, sum, s, nxt);
+    }
+}
+
+// ================================================================ selector
+__device__ __forceinline__ float bf16f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+// One warp: 8 -> 32 -> 32 -> 3 MLP, BF16 weights, FP32 accumulation.
+__device__ int mlp_mode(const SelectorDev* S, const float* f) {
+    const uint32_t j = lane_id();
+    float xn[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) xn[i] = (f[i] - S->mu[i]) / S->sd[i];
+    float h1 = S->b1[j];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h1 = fmaf(bf16f(S->W1[j * 8 + i]), xn[i], h1);
+    h1 = fmaxf(h1, 0.f);
+    float h2 = S->b2[j];
+    for (int k = 0; k < 32; ++k) h2 = fmaf(bf16f(S->W2[j * 32 + k]), __shfl_sync(FULL, h1, k), h2);
+    h2 = fmaxf(h2, 0.f);
+    float z[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        float p = bf16f(S->W3[m * 32 + j]) * h2;
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
+        z[m] = p + S->b3[m];
+    }
+    int best = 0;
+    if (z[1] > z[best]) best = 1;
+    if (z[2] > z[best]) best = 2;
+    return best;
+}
+
+__global__ void k_select(Params P) {
+    DevCtl* c = P.ctl;
+    const uint32_t s = c->superstep;
+    uint32_t act, bc, maxd;
+    unsigned long long msgs;
+    if (P.app == APP_PR) {
+        const bool b = s < P.T;
+        act = P.V;
+        bc = b ? P.V : 0;
+        msgs = b ? P.E : 0;
+        maxd = b ? P.max_out_deg : 0;
+    } else {
+        act = c->n_active;
+        bc = c->n_bcast;
+        msgs = c->msgs;
+        maxd = c->max_deg;
+    }
+    const uint64_t now = globaltimer();
+    const float dt = s == 0 ? 0.f : (float)(now - c->t_prev);
+    float f[N_FEATURES];
+    f[0] = log1pf((float)bc);
+    f[1] = log1pf((float)msgs);
+    f[2] = log1pf(bc ? (float)((double)msgs / bc) : 0.f);
+    f[3] = log1pf((float)maxd);
+    f[4] = (float)bc / (float)P.V;
+    f[5] = log1pf(dt);
+    f[6] = P.E ? (float)((double)msgs / (double)P.E) : 0.f;
+    f[7] = logf(((float)bc + 1.f) / ((float)c->prev_bcast + 1.f));
+    uint32_t done;
+    if (P.app == APP_PR)
+        done = s >= P.T ? 1u : 0u;
+    else
+        done = msgs == 0 ? 1u : 0u;
+    if (!done && s + 1 >= P.max_supersteps) done = 2;
+    int mode;
+    switch (P.policy) {
+        case IP_POLICY_FORCED: mode = P.forced_mode; break;
+        case IP_POLICY_SEQUENCE: mode = P.seq[s % P.seq_len]; break;
+        case IP_POLICY_MLP: mode = mlp_mode(P.sel, f); break;
+        default:
+            mode = f[6] < P.thr_sparse ? IP_MODE_PUSH_SPARSE : (f[6] >= P.thr_pull ? IP_MODE_PULL : IP_MODE_PUSH_DENSE);
+    }
+    if (P.app == APP_PR && mode == IP_MODE_PUSH_SPARSE) mode = IP_MODE_PUSH_DENSE;  // every vertex broadcasts
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        if (s < P.log_cap) {
+            LogRec r;
+            r.mode = c->mode_used;
+            r.active = act;
+            r.bcast = bc;
+            r.max_deg = maxd;
+            r.msgs = msgs;
+            for (int i = 0; i < N_FEATURES; ++i) r.feat[i] = f[i];
+            P.log[s] = r;
+        }
+        c->mode = (unsigned)mode;
+        c->done = done;
+        c->prev_bcast = bc;
+        c->t_prev = now;
+        if (!done) {
+            const uint32_t s1 = s + 1;
+            c->superstep = s1;
+            c->mode_used = (unsigned)mode;
+            c->n_active = 0;
+            c->n_bcast = 0;
+            c->msgs = 0;
+            c->max_deg = 0;
+            c->rq_len = 0;
+            c->bq_len[s1 & 1] = 0;
+            c->hq_len[s1 & 1] = 0;
+        }
+        if (P.use_graph) {
+            cudaGraphSetConditional(P.h_switch, (unsigned)mode);
+            cudaGraphSetConditional(P.h_while, done ? 0u : 1u);
+        }
+    }
+}
+
+// ================================================================ host side
+namespace {
+
+int grid_of(const ip_graph* g, const void* fn) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BLOCK, 0) != cudaSuccess || occ < 1) {
+        (void)cudaGetLastError();
+        occ = 2;
+    }
+    return g->num_sms * occ;
+}
+
+enum { G_PR_PULL, G_PR_PUSH, G_PUSH_HM_S, G_PUSH_SSSP_S, G_PUSH_HM_D, G_PUSH_SSSP_D, G_PULL_HM, G_PULL_SSSP, G_MISC, G_COUNT };
+
+// Grid sizes (resident CTAs per SM x SMs), queried once per handle, outside any capture.
+void compute_grids(ip_graph* g) {
+    if (g->grids_ready) return;
+    const void* fns[G_COUNT] = {(const void*)k_pr_pull, (const void*)k_pr_push, (const void*)k_push<APP_HM, true>,
+                                (const void*)k_push<APP_SSSP, true>, (const void*)k_push<APP_HM, false>,
+                                (const void*)k_push<APP_SSSP, false>, (const void*)k_pull<APP_HM>,
+                                (const void*)k_pull<APP_SSSP>, nullptr};
+    for (int i = 0; i < G_COUNT; ++i) g->grid[i] = fns[i] ? grid_of(g, fns[i]) : g->num_sms * 4;
+    g->grids_ready = true;
+}
+
+// Exchange + apply of one superstep in the given mode.
+int launch_superstep(const ip_graph* g, const Params& P, int mode, cudaStream_t st) {
+    const int* G = g->grid;
+    if (P.app == APP_PR) {
+        if (mode == IP_MODE_PULL) {
+            k_pr_pull<<<G[G_PR_PULL], BLOCK, 0, st>>>(P);
+        } else {
+            k_pr_push<<<G[G_PR_PUSH], BLOCK, 0, st>>>(P);
+            k_pr_apply<<<G[G_MISC], BLOCK, 0, st>>>(P);
+        }
+        return cuda_err(cudaGetLastError());
+    }
+    const bool hm = P.app == APP_HM;
+    switch (mode) {
+        case IP_MODE_PUSH_SPARSE:
+            k_compact<<<G[G_MISC], BLOCK, 0, st>>>(P);
+            if (hm)
+                k_push<APP_HM, true><<<G[G_PUSH_HM_S], BLOCK, 0, st>>>(P);
+            else
+                k_push<APP_SSSP, true><<<G[G_PUSH_SSSP_S], BLOCK, 0, st>>>(P);
+            k_apply_queue<<<G[G_MISC], BLOCK, 0, st>>>(P);
+            break;
+        case IP_MODE_PUSH_DENSE:
+            if (hm)
+                k_push<APP_HM, false><<<G[G_PUSH_HM_D], BLOCK, 0, st>>>(P);
+            else
+                k_push<APP_SSSP, false><<<G[G_PUSH_SSSP_D], BLOCK, 0, st>>>(P);
+            k_apply_bitmap<<<G[G_MISC], BLOCK, 0, st>>>(P);
+            break;
+        default:
+            if (hm)
+                k_pull<APP_HM><<<G[G_PULL_HM], BLOCK, 0, st>>>(P);
+            else
+                k_pull<APP_SSSP><<<G[G_PULL_SSSP], BLOCK, 0, st>>>(P);
+            k_apply_bitmap<<<G[G_MISC], BLOCK, 0, st>>>(P);
+            break;
+    }
+    return cuda_err(cudaGetLastError());
+}
+
+int launch_init(const ip_graph* g, const Params& P, cudaStream_t st) {
+    const int gmisc = g->grid[G_MISC];
+    if (P.app == APP_PR)
+        k_pr_init<<<gmisc, BLOCK, 0, st>>>(P);
+    else
+        k_init_min<<<gmisc, BLOCK, 0, st>>>(P);
+    k_select<<<1, 32, 0, st>>>(P);
+    return cuda_err(cudaGetLastError());
+}
+
+#define CKR(x)                       \
+    do {                             \
+        int _r = (x);                \
+        if (_r != IP_OK) return _r;  \
+    } while (0)
+
+int read_ctl(ip_graph* g, cudaStream_t st) {
+    CKR(cuda_err(cudaMemcpyAsync(g->ctl_host, g->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st)));
+    return cuda_err(cudaStreamSynchronize(st));
+}
+
+int host_loop(ip_graph* g, const Params& P, cudaStream_t st) {
+    CKR(launch_init(g, P, st));
+    CKR(read_ctl(g, st));
+    while (!g->ctl_host->done) {
+        CKR(launch_superstep(g, P, (int)g->ctl_host->mode, st));
+        k_select<<<1, 32, 0, st>>>(P);
+        CKR(cuda_err(cudaGetLastError()));
+        CKR(read_ctl(g, st));
+    }
+    return IP_OK;
+}
+
+// Host loop that, before each exchange, times every mode from the same state.
+int label_loop(ip_graph* g, const Params& P, cudaStream_t st, ip_run_stats_t* stats) {
+    if (!g->snap_value) {
+        CKR(alloc_dev(g, (void**)&g->snap_value, (size_t)g->V * 4));
+        CKR(alloc_dev(g, (void**)&g->snap_bcast, (size_t)g->W * 4));
+    }
+    DevCtl snap_ctl;
+    CKR(launch_init(g, P, st));
+    CKR(read_ctl(g, st));
+    while (!g->ctl_host->done) {
+        const int chosen = (int)g->ctl_host->mode;
+        const uint32_t s1 = g->ctl_host->superstep;  // the superstep about to run
+        int order[3], no = 0;
+        const int nmodes = 3;
+        for (int m = 0; m < nmodes; ++m)
+            if (m != chosen) order[no++] = m;
+        order[no++] = chosen;
+        snap_ctl = *g->ctl_host;
+        if (P.app != APP_PR) {
+            CKR(cuda_err(cudaMemcpyAsync(g->snap_value, g->value, (size_t)g->V * 4, cudaMemcpyDeviceToDevice, st)));
+            CKR(cuda_err(cudaMemcpyAsync(g->snap_bcast, g->bcast, (size_t)g->W * 4, cudaMemcpyDeviceToDevice, st)));
+        }
+        for (int k = 0; k < no; ++k) {
+            const int m = order[k];
+            if (k > 0) {  // restore the pre-exchange state
+                CKR(cuda_err(cudaMemcpyAsync(g->ctl, &snap_ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st)));
+                if (P.app != APP_PR) {
+                    CKR(cuda_err(cudaMemcpyAsync(g->value, g->snap_value, (size_t)g->V * 4, cudaMemcpyDeviceToDevice, st)));
+                    CKR(cuda_err(cudaMemcpyAsync(g->bcast, g->snap_bcast, (size_t)g->W * 4, cudaMemcpyDeviceToDevice, st)));
+                }
+            }
+            CKR(cuda_err(cudaEventRecord(g->ev0, st)));
+            CKR(launch_superstep(g, P, m, st));
+            CKR(cuda_err(cudaEventRecord(g->ev1, st)));
+            CKR(cuda_err(cudaStreamSynchronize(st)));
+            float ms = 0.f;
+            CKR(cuda_err(cudaEventElapsedTime(&ms, g->ev0, g->ev1)));
+            if (stats && stats->mode_ms && s1 < stats->capacity) stats->mode_ms[3 * s1 + m] = ms;
+        }
+        k_select<<<1, 32, 0, st>>>(P);
+        CKR(cuda_err(cudaGetLastError()));
+        CKR(read_ctl(g, st));
+    }
+    return IP_OK;
+}
+
+}  // namespace
+
+void free_graph_exec(ip_graph* g) {
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    g->gexec = nullptr;
+    g->graph = nullptr;
+    g->has_gkey = false;
+}
+
+namespace {
+
+// Adds a conditional node at the current capture position of st and makes it the
+// new capture dependency. Returns its body graphs through params.
+int add_conditional(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, unsigned size,
+                    cudaGraph_t** bodies) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CKR(cuda_err(cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &ndeps)));
+    if (cs != cudaStreamCaptureStatusActive) return IP_E_CUDA;
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = type;
+    np.conditional.size = size;
+    cudaGraphNode_t node;
+    CKR(cuda_err(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &np)));
+    CKR(cuda_err(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies)));
+    *bodies = np.conditional.phGraph_out;
+    return IP_OK;
+}
+
+// Whole run as one graph: init, select, then while(continue){ switch(mode){...}; select }.
+int build_graph(ip_graph* g, Params P, cudaStream_t st) {
+    free_graph_exec(g);
+    cudaStream_t cap;
+    CKR(cuda_err(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)));
+    int r = IP_OK;
+    cudaGraph_t graph = nullptr;
+    do {
+        r = cuda_err(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        if (r) break;
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg;
+        r = cuda_err(cudaStreamGetCaptureInfo(cap, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+        if (!r) r = cuda_err(cudaGraphConditionalHandleCreate(&P.h_while, cg, 0, cudaGraphCondAssignDefault));
+        if (!r) r = cuda_err(cudaGraphConditionalHandleCreate(&P.h_switch, cg, 0, cudaGraphCondAssignDefault));
+        if (!r) r = launch_init(g, P, cap);
+        cudaGraph_t* wbody = nullptr;
+        if (!r) r = add_conditional(cap, P.h_while, cudaGraphCondTypeWhile, 1, &wbody);
+        cudaGraph_t captured = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cap, &captured);
+        if (!r) r = cuda_err(e);
+        if (r) {
+            if (captured) cudaGraphDestroy(captured);
+            break;
+        }
+        graph = captured;
+        // while body: switch node then select
+        r = cuda_err(cudaStreamBeginCaptureToGraph(cap, wbody[0], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        if (r) break;
+        cudaGraph_t* sbody = nullptr;
+        r = add_conditional(cap, P.h_switch, cudaGraphCondTypeSwitch, 3, &sbody);
+        if (!r) {
+            k_select<<<1, 32, 0, cap>>>(P);
+            r = cuda_err(cudaGetLastError());
+        }
+        cudaGraph_t tmp = nullptr;
+        e = cudaStreamEndCapture(cap, &tmp);
+        if (!r) r = cuda_err(e);
+        if (r) break;
+        for (int m = 0; m < 3 && !r; ++m) {
+            r = cuda_err(cudaStreamBeginCaptureToGraph(cap, sbody[m], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            if (r) break;
+            r = launch_superstep(g, P, m, cap);
+            e = cudaStreamEndCapture(cap, &tmp);
+            if (!r) r = cuda_err(e);
+        }
+    } while (0);
+    if (!r) r = cuda_err(cudaGraphInstantiate(&g->gexec, graph, 0));
+    cudaStreamDestroy(cap);
+    if (r) {
+        if (graph) cudaGraphDestroy(graph);
+        g->gexec = nullptr;
+        (void)cudaGetLastError();
+        return r;
+    }
+    g->graph = graph;
+    return IP_OK;
+}
+
+}  // namespace
+
+int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* opt, ip_run_stats_t* stats) {
+    ip_options_t o;
+    if (opt)
+        o = *opt;
+    else
+        ip_options_default(&o);
+    cudaStream_t st = (cudaStream_t)o.stream;
+    if (app == APP_SSSP && o.source >= g->V) return IP_E_RANGE;
+    if (o.policy < IP_POLICY_AUTO || o.policy > IP_POLICY_SEQUENCE) return IP_E_INVAL;
+    if (o.policy == IP_POLICY_FORCED && (o.forced_mode < 0 || o.forced_mode > 2)) return IP_E_INVAL;
+    if (o.policy == IP_POLICY_SEQUENCE) {
+        if (!o.mode_sequence || o.mode_sequence_len == 0 || o.mode_sequence_len > MAX_SEQ) return IP_E_INVAL;
+        for (uint32_t i = 0; i < o.mode_sequence_len; ++i)
+            if (o.mode_sequence[i] > 2) return IP_E_INVAL;
+    }
+    if (o.policy == IP_POLICY_MLP && !g->has_selector) return IP_E_STATE;
+    if (app == APP_PR && !(o.damping >= 0.f && o.damping <= 1.f)) return IP_E_INVAL;
+    const uint32_t t1 = o.t1 ? o.t1 : DEFAULT_T1;
+    const uint32_t t2 = o.t2 ? o.t2 : DEFAULT_T2;
+    if (t1 >= t2) return IP_E_INVAL;
+    CKR(ensure_bins(g, t2, st));
+    compute_grids(g);
+
+    const uint32_t want_log = std::min<uint32_t>(max_supersteps, 1u << 16);
+    if (g->log_cap < want_log) {
+        if (g->log) cudaFree(g->log);
+        g->log = nullptr;
+        g->log_cap = 0;
+        CKR(alloc_dev(g, (void**)&g->log, (size_t)want_log * sizeof(LogRec)));
+        g->log_cap = want_log;
+        free_graph_exec(g);
+    }
+
+    Params P;
+    memset(&P, 0, sizeof(P));
+    P.V = g->V;
+    P.W = g->W;
+    P.E = g->E;
+    P.csr_off = g->csr_off;
+    P.csr_col = g->csr_col;
+    P.csr_w = g->csr_w;
+    P.csc_off = g->csc_off;
+    P.csc_row = g->csc_row;
+    P.csc_w = g->csc_w;
+    P.heavy_out = g->heavy_out;
+    P.heavy_in = g->heavy_in;
+    P.n_heavy_out = g->n_heavy_out;
+    P.n_heavy_in = g->n_heavy_in;
+    P.inv_outdeg = g->inv_outdeg;
+    P.value = g->value;
+    P.rank = g->rank;
+    P.contrib0 = g->contrib[0];
+    P.contrib1 = g->contrib[1];
+    P.mbox = g->mbox;
+    P.mboxf = g->mboxf;
+    P.recv = g->recv;
+    P.bcast = g->bcast;
+    P.rq = g->rq;
+    P.bq0 = g->bq[0];
+    P.bq1 = g->bq[1];
+    P.hq0 = g->hq[0];
+    P.hq1 = g->hq[1];
+    P.ctl = g->ctl;
+    P.log = g->log;
+    P.log_cap = g->log_cap;
+    P.sel = g->sel;
+    P.t1 = t1;
+    P.t2 = t2;
+    P.thr_sparse = o.thr_sparse;
+    P.thr_pull = o.thr_pull;
+    P.app = (uint32_t)app;
+    P.T = o.pr_iterations;
+    P.source = o.source;
+    P.max_supersteps = max_supersteps;
+    P.damping = o.damping;
+    P.pr_base = (float)((1.0 - (double)o.damping) / (double)g->V);
+    P.policy = o.policy == IP_POLICY_AUTO ? (g->has_selector ? IP_POLICY_MLP : IP_POLICY_THRESHOLD) : o.policy;
+    P.forced_mode = o.forced_mode;
+    P.seq_len = o.policy == IP_POLICY_SEQUENCE ? o.mode_sequence_len : 1;
+    if (o.policy == IP_POLICY_SEQUENCE) memcpy(P.seq, o.mode_sequence, o.mode_sequence_len);
+    P.max_out_deg = g->max_out_deg;
+    if (app == APP_SSSP) {
+        uint32_t two[2];
+        CKR(cuda_err(cudaMemcpyAsync(two, g->csr_off + o.source, 8, cudaMemcpyDeviceToHost, st)));
+        CKR(cuda_err(cudaStreamSynchronize(st)));
+        P.out_deg_src = two[1] - two[0];
+    }
+    const bool use_graph = o.use_graph && !o.collect_labels;
+    P.use_graph = use_graph ? 1 : 0;
+
+    if (stats && stats->mode_ms && stats->capacity) memset(stats->mode_ms, 0, sizeof(float) * 3 * stats->capacity);
+    CKR(cuda_err(cudaEventRecord(g->ev0, st)));
+    int r;
+    if (o.collect_labels) {
+        r = label_loop(g, P, st, stats);
+    } else if (use_graph) {
+        // the graph bakes the kernel parameters; rebuild when they change
+        Params key = P;
+        key.h_while = key.h_switch = 0;
+        if (!g->has_gkey || memcmp(g->gkey, &key, sizeof(Params)) != 0 || !g->gexec) {
+            r = build_graph(g, P, st);
+            if (r) return r;
+            memcpy(g->gkey, &key, sizeof(Params));
+            g->has_gkey = true;
+        }
+        r = cuda_err(cudaGraphLaunch(g->gexec, st));
+        if (!r) r = read_ctl(g, st);
+    } else {
+        r = host_loop(g, P, st);
+    }
+    if (r) return r;
+    CKR(cuda_err(cudaEventRecord(g->ev1, st)));
+    CKR(cuda_err(cudaEventSynchronize(g->ev1)));
+    float elapsed = 0.f;
+    CKR(cuda_err(cudaEventElapsedTime(&elapsed, g->ev0, g->ev1)));
+    CKR(read_ctl(g, st));
+    const DevCtl& c = *g->ctl_host;
+    const uint32_t supersteps = c.superstep + 1;
+    g->last_app = app;
+    if (c.err) return IP_E_DEVICE_ASSERT;
+    if (stats) {
+        stats->supersteps = supersteps;
+        stats->halted = c.done == 1 ? 1 : 0;
+        stats->elapsed_ms = elapsed;
+        const uint32_t n = std::min(std::min(supersteps, stats->capacity), g->log_cap);
+        if (n) {
+            LogRec* h = (LogRec*)malloc(sizeof(LogRec) * n);
+            if (!h) return IP_E_NOMEM;
+            cudaError_t e = cudaMemcpy(h, g->log, sizeof(LogRec) * n, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                free(h);
+                return cuda_err(e);
+            }
+            for (uint32_t i = 0; i < n; ++i) {
+                if (stats->mode) stats->mode[i] = (uint8_t)h[i].mode;
+                if (stats->active) stats->active[i] = h[i].active;
+                if (stats->broadcasters) stats->broadcasters[i] = h[i].bcast;
+                if (stats->messages) stats->messages[i] = h[i].msgs;
+                if (stats->features)
+                    for (int k = 0; k < N_FEATURES; ++k) stats->features[i * N_FEATURES + k] = h[i].feat[k];
+            }
+            free(h);
+        }
+    }
+    return c.done == 1 ? IP_OK : IP_E_MAXSTEPS;
+}
+
+}  // namespace ipg
