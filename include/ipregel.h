@@ -92,6 +92,8 @@ typedef struct {
                                      0: the host drives the loop, one 4-byte readback per superstep */
     int32_t collect_labels;       /* 1: also time all three modes in every superstep (host loop);
                                      fills ip_run_stats_t.mode_ms. Values are unchanged. */
+    int32_t profile_kernels;      /* 1: host loop with CUDA events around every kernel; fills
+                                     ip_run_stats_t.kernel_ms. Values are unchanged. */
     void* stream;                 /* cudaStream_t */
 } ip_options_t;
 
@@ -110,6 +112,9 @@ typedef struct {
     float* features;       /* [8*s + i]: selector input computed after superstep s */
     float* mode_ms;        /* [3*s + m]: milliseconds of mode m delivering into superstep s
                               (collect_labels only; 0 otherwise) */
+    float* kernel_ms;      /* [4*s + k]: milliseconds of the kernels that computed superstep s:
+                              k = 0 queue compaction, 1 exchange, 2 apply, 3 selector
+                              (profile_kernels only; 0 for kernels that did not run) */
     float elapsed_ms;      /* device time of the whole run (init to halt) */
 } ip_run_stats_t;
 

@@ -49,14 +49,15 @@ class Options(ctypes.Structure):
                 ("mode_sequence", ctypes.POINTER(ctypes.c_uint8)), ("mode_sequence_len", ctypes.c_uint32),
                 ("t1", ctypes.c_uint32), ("t2", ctypes.c_uint32), ("thr_sparse", ctypes.c_float),
                 ("thr_pull", ctypes.c_float), ("use_graph", ctypes.c_int32), ("collect_labels", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("profile_kernels", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class RunStatsC(ctypes.Structure):
     _fields_ = [("supersteps", ctypes.c_uint32), ("halted", ctypes.c_int32), ("capacity", ctypes.c_uint32),
                 ("mode", ctypes.POINTER(ctypes.c_uint8)), ("active", _U32P), ("broadcasters", _U32P),
                 ("messages", ctypes.POINTER(ctypes.c_uint64)), ("features", ctypes.POINTER(ctypes.c_float)),
-                ("mode_ms", ctypes.POINTER(ctypes.c_float)), ("elapsed_ms", ctypes.c_float)]
+                ("mode_ms", ctypes.POINTER(ctypes.c_float)), ("kernel_ms", ctypes.POINTER(ctypes.c_float)),
+                ("elapsed_ms", ctypes.c_float)]
 
 
 class GraphInfo(ctypes.Structure):
@@ -171,6 +172,7 @@ class RunStats:
     messages: np.ndarray
     features: np.ndarray
     mode_ms: np.ndarray
+    kernel_ms: np.ndarray
 
 
 class Graph:
@@ -234,7 +236,8 @@ class Graph:
         cap = stats_capacity
         arr = dict(mode=np.zeros(cap, np.uint8), active=np.zeros(cap, np.uint32),
                    broadcasters=np.zeros(cap, np.uint32), messages=np.zeros(cap, np.uint64),
-                   features=np.zeros(cap * N_FEATURES, np.float32), mode_ms=np.zeros(cap * 3, np.float32))
+                   features=np.zeros(cap * N_FEATURES, np.float32), mode_ms=np.zeros(cap * 3, np.float32),
+                   kernel_ms=np.zeros(cap * 4, np.float32))
         s = RunStatsC()
         s.capacity = cap
         s.mode = arr["mode"].ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
@@ -243,13 +246,14 @@ class Graph:
         s.messages = arr["messages"].ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
         s.features = arr["features"].ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         s.mode_ms = arr["mode_ms"].ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        s.kernel_ms = arr["kernel_ms"].ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         code = load().ip_run(self._h, app, int(max_supersteps), ctypes.byref(o), ctypes.byref(s))
         if code not in (IP_OK, IP_E_MAXSTEPS) or (raise_on_maxsteps and code == IP_E_MAXSTEPS):
             raise IPError(code, "ip_run")
         n = min(s.supersteps, cap)
         return RunStats(code, s.supersteps, bool(s.halted), s.elapsed_ms, arr["mode"][:n], arr["active"][:n],
                         arr["broadcasters"][:n], arr["messages"][:n], arr["features"].reshape(cap, N_FEATURES)[:n],
-                        arr["mode_ms"].reshape(cap, 3)[:n])
+                        arr["mode_ms"].reshape(cap, 3)[:n], arr["kernel_ms"].reshape(cap, 4)[:n])
 
     def values(self, app=None, out=None, stream=None):
         """Values of the last run: float32 ranks or uint32 labels/distances.

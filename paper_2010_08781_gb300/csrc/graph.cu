@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "internal.h"
 
@@ -160,48 +161,110 @@ __global__ void k_scatter_in(const uint32_t* csr_off, const uint32_t* col, const
     }
 }
 
-__global__ void k_heavy_list(const uint32_t* off, uint32_t n, uint32_t t2, uint32_t* list, unsigned int* count) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        if (off[v + 1] - off[v] >= t2) list[atomicAdd(count, 1u)] = v;
-    }
-}
-
 // ------------------------------------------------------------------ helpers
-static int grid_for(ip_graph* g, uint64_t work) {
+static int grid_for(const ip_graph* g, uint64_t work) {
     uint64_t b = (work + 255) / 256;
     uint64_t cap = (uint64_t)g->num_sms * 16;
     if (b > cap) b = cap;
     return (int)(b ? b : 1);
 }
 
-int ensure_bins(ip_graph* g, uint32_t t2, cudaStream_t st) {
-    if (g->bins_t2 == t2) return IP_OK;
-    unsigned int* cnt = &g->ctl->err;  // borrow: reset below
-    unsigned int zero[2] = {0, 0};
-    unsigned int h[2];
-    uint32_t* lists[2] = {g->heavy_out, g->heavy_in};
-    const uint32_t* offs[2] = {g->csr_off, g->csc_off};
-    for (int k = 0; k < 2; ++k) {
-        CK(cudaMemcpyAsync(cnt, zero, sizeof(unsigned int), cudaMemcpyHostToDevice, st));
-        k_heavy_list<<<grid_for(g, g->V), 256, 0, st>>>(offs[k], g->V, t2, lists[k], cnt);
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(&h[k], cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+static void free_bins(ip_graph* g, int k) {
+    for (int i = 0; i < 5; ++i) {
+        if (g->bin_mem[k][i]) {
+            cudaFree(g->bin_mem[k][i]);
+            g->device_bytes -= g->bin_bytes[k][i];
+        }
+        g->bin_mem[k][i] = nullptr;
+        g->bin_bytes[k][i] = 0;
     }
-    CK(cudaMemcpyAsync(cnt, zero, sizeof(unsigned int), cudaMemcpyHostToDevice, st));
+    g->bins[k] = Bins{};
+}
+
+static int bin_alloc(ip_graph* g, int k, int i, size_t bytes) {
+    bytes = bytes ? bytes : 16;
+    int r = alloc_dev(g, &g->bin_mem[k][i], bytes);
+    if (!r) g->bin_bytes[k][i] = bytes;
+    return r;
+}
+
+// Static degree bins of one direction, built on the host from the offsets.
+static int build_bins(ip_graph* g, int k, const uint32_t* dev_off, uint32_t t1, uint32_t t2, cudaStream_t st) {
+    const uint32_t n = g->V;
+    std::vector<uint32_t> off((size_t)n + 1);
+    CK(cudaMemcpyAsync(off.data(), dev_off, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    g->n_heavy_out = h[0];
-    g->n_heavy_in = h[1];
-    g->bins_t2 = t2;
+    std::vector<uint32_t> med;
+    std::vector<uint4> chunks;
+    std::vector<uint2> hv;
+    for (uint32_t v = 0; v < n; ++v) {
+        const uint32_t b = off[v], e = off[v + 1], d = e - b;
+        if (d > t1 && d < t2) {
+            med.push_back(v);
+        } else if (d >= t2) {
+            const uint32_t nch = (d + HCH - 1) / HCH;
+            hv.push_back(make_uint2((uint32_t)chunks.size(), nch));
+            for (uint32_t c = 0; c < nch; ++c) {
+                const uint32_t cb = b + c * HCH;
+                const uint32_t ce = (e - cb) > HCH ? cb + HCH : e;
+                chunks.push_back(make_uint4(v, cb, ce, (uint32_t)hv.size() - 1));
+            }
+        }
+    }
+    free_bins(g, k);
+    Bins& B = g->bins[k];
+    void** mem = g->bin_mem[k];
+    int r;
+    const size_t sz[5] = {med.size() * 4, chunks.size() * 16, hv.size() * 8, hv.size() * 4, chunks.size() * 8};
+    for (int i = 0; i < 5; ++i) {
+        if ((r = bin_alloc(g, k, i, sz[i]))) return r;
+    }
+    if (!med.empty()) CK(cudaMemcpyAsync(mem[0], med.data(), sz[0], cudaMemcpyHostToDevice, st));
+    if (!chunks.empty()) CK(cudaMemcpyAsync(mem[1], chunks.data(), sz[1], cudaMemcpyHostToDevice, st));
+    if (!hv.empty()) CK(cudaMemcpyAsync(mem[2], hv.data(), sz[2], cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(mem[3], 0, sz[3] ? sz[3] : 16, st));
+    CK(cudaStreamSynchronize(st));
+    B.med = (const uint32_t*)mem[0];
+    B.n_med = (uint32_t)med.size();
+    B.hchunk = (const uint4*)mem[1];
+    B.n_hchunk = (uint32_t)chunks.size();
+    B.hvert = (const uint2*)mem[2];
+    B.n_hvert = (uint32_t)hv.size();
+    B.hcnt = (uint32_t*)mem[3];
+    B.hpart = (float2*)mem[4];
     return IP_OK;
 }
 
-static int validate_host(uint32_t n, uint64_t E, const uint32_t* off, const uint32_t* ids) {
-    if (off[0] != 0 || (uint64_t)off[n] != E) return IP_E_INVAL;
-    for (uint32_t v = 0; v < n; ++v)
-        if (off[v + 1] < off[v]) return IP_E_INVAL;
-    for (uint64_t i = 0; i < E; ++i)
-        if (ids[i] >= n) return IP_E_RANGE;
+int ensure_bins(ip_graph* g, uint32_t t1, uint32_t t2, cudaStream_t st) {
+    if (g->bins_t1 == t1 && g->bins_t2 == t2) return IP_OK;
+    g->bins_t1 = g->bins_t2 = 0;
+    int r;
+    if ((r = build_bins(g, 0, g->csr_off, t1, t2, st))) return r;
+    if (g->csc_alias) {
+        free_bins(g, 1);
+        // share the CSR bins except the PageRank finish state, which must be private
+        g->bins[1] = g->bins[0];
+        if ((r = bin_alloc(g, 1, 3, g->bins[0].n_hvert * 4 + 16))) return r;
+        if ((r = bin_alloc(g, 1, 4, g->bins[0].n_hchunk * 8 + 16))) return r;
+        CK(cudaMemsetAsync(g->bin_mem[1][3], 0, g->bins[0].n_hvert * 4 + 16, st));
+        g->bins[1].hcnt = (uint32_t*)g->bin_mem[1][3];
+        g->bins[1].hpart = (float2*)g->bin_mem[1][4];
+    } else if ((r = build_bins(g, 1, g->csc_off, t1, t2, st))) {
+        return r;
+    }
+    // heavy broadcaster queues hold at most every heavy CSR chunk once
+    for (int p = 0; p < 2; ++p) {
+        if (g->hq[p]) {
+            cudaFree(g->hq[p]);
+            g->device_bytes -= (size_t)(g->hq_cap + 1) * sizeof(uint2);
+            g->hq[p] = nullptr;
+        }
+    }
+    g->hq_cap = g->bins[0].n_hchunk;
+    for (int p = 0; p < 2; ++p)
+        if ((r = alloc_dev(g, (void**)&g->hq[p], (size_t)(g->hq_cap + 1) * sizeof(uint2)))) return r;
+    g->bins_t1 = t1;
+    g->bins_t2 = t2;
     return IP_OK;
 }
 
@@ -248,17 +311,12 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
     CK(cudaMallocHost((void**)&g->ctl_host, sizeof(DevCtl)));
 
     const bool alias = csc_off != nullptr && csc_off == csr_off && csc_row == csr_col;
-    if (!device_ptrs) {
-        if ((r = validate_host(n, E, csr_off, csr_col))) return r;
-        if (csc_off && !alias && (r = validate_host(n, E, csc_off, csc_row))) return r;
-    }
     const size_t ea = edge_alloc_count(E);
     if ((r = upload(g, &g->csr_off, csr_off, (size_t)n + 1, (size_t)n + 1, device_ptrs, st))) return r;
     if ((r = upload(g, &g->csr_col, csr_col, E, ea, device_ptrs, st))) return r;
     if (csr_w && (r = upload(g, &g->csr_w, csr_w, E, ea, device_ptrs, st))) return r;
-    if (device_ptrs) {
-        if ((r = validate_device(g, g->csr_off, g->csr_col, st))) return r;
-    }
+    // validated on the device whether the caller's arrays were host or device memory
+    if ((r = validate_device(g, g->csr_off, g->csr_col, st))) return r;
     if (alias) {
         g->csc_alias = true;
         g->csc_off = g->csr_off;
@@ -268,7 +326,7 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
         if ((r = upload(g, &g->csc_off, csc_off, (size_t)n + 1, (size_t)n + 1, device_ptrs, st))) return r;
         if ((r = upload(g, &g->csc_row, csc_row, E, ea, device_ptrs, st))) return r;
         if (csc_w && (r = upload(g, &g->csc_w, csc_w, E, ea, device_ptrs, st))) return r;
-        if (device_ptrs && (r = validate_device(g, g->csc_off, g->csc_row, st))) return r;
+        if ((r = validate_device(g, g->csc_off, g->csc_row, st))) return r;
     } else {
         // transpose on the device: count, scan, scatter
         if ((r = alloc_dev(g, (void**)&g->csc_off, ((size_t)n + 1) * sizeof(uint32_t)))) return r;
@@ -308,19 +366,18 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
     if ((r = alloc_dev(g, (void**)&g->contrib[0], nv * 4))) return r;
     if ((r = alloc_dev(g, (void**)&g->contrib[1], nv * 4))) return r;
     if ((r = alloc_dev(g, (void**)&g->mbox, nv * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->outbox, nv * 4))) return r;
     if ((r = alloc_dev(g, (void**)&g->mboxf, nv * 4))) return r;
     if ((r = alloc_dev(g, (void**)&g->recv, (size_t)g->W * 4))) return r;
-    if ((r = alloc_dev(g, (void**)&g->bcast, (size_t)g->W * 4))) return r;
     if ((r = alloc_dev(g, (void**)&g->rq, nv * 4))) return r;
     for (int k = 0; k < 2; ++k) {
-        if ((r = alloc_dev(g, (void**)&g->bq[k], nv * 4))) return r;
-        if ((r = alloc_dev(g, (void**)&g->hq[k], nv * 4))) return r;
+        if ((r = alloc_dev(g, (void**)&g->bcast[k], (size_t)g->W * 4))) return r;
+        CK(cudaMemsetAsync(g->bcast[k], 0, (size_t)g->W * 4, st));
+        for (int b = 0; b < 2; ++b)
+            if ((r = alloc_dev(g, (void**)&g->q[k][b], nv * 4))) return r;
     }
-    if ((r = alloc_dev(g, (void**)&g->heavy_out, nv * 4))) return r;
-    if ((r = alloc_dev(g, (void**)&g->heavy_in, nv * 4))) return r;
     if ((r = alloc_dev(g, (void**)&g->sel, sizeof(SelectorDev)))) return r;
     CK(cudaMemsetAsync(g->recv, 0, (size_t)g->W * 4, st));
-    CK(cudaMemsetAsync(g->bcast, 0, (size_t)g->W * 4, st));
 
     unsigned int* mx = &g->ctl->err;
     CK(cudaMemsetAsync(mx, 0, 4, st));
@@ -334,8 +391,8 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
     CK(cudaMemcpyAsync(&g->max_in_deg, mx, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaMemsetAsync(mx, 0, 4, st));
-    g->bins_t2 = 0;
-    if ((r = ensure_bins(g, DEFAULT_T2, st))) return r;
+    g->bins_t1 = g->bins_t2 = 0;
+    if ((r = ensure_bins(g, DEFAULT_T1, DEFAULT_T2, st))) return r;
     CK(cudaEventCreate(&g->ev0));
     CK(cudaEventCreate(&g->ev1));
     CK(cudaStreamSynchronize(st));
@@ -368,11 +425,15 @@ void ip_options_default(ip_options_t* o) {
 void ip_graph_destroy(ip_graph_t* g) {
     if (!g) return;
     free_graph_exec(g);
-    void* bufs[] = {g->ctl, g->csr_off, g->csr_col, g->csr_w, g->inv_outdeg, g->value, g->rank, g->contrib[0],
-                    g->contrib[1], g->mbox, g->mboxf, g->recv, g->bcast, g->rq, g->bq[0], g->bq[1], g->hq[0],
-                    g->hq[1], g->heavy_out, g->heavy_in, g->log, g->sel, g->snap_value, g->snap_bcast};
+    void* bufs[] = {g->ctl,        g->csr_off,    g->csr_col, g->csr_w,      g->inv_outdeg, g->value,
+                    g->rank,       g->contrib[0], g->contrib[1], g->mbox,  g->mboxf,      g->recv, g->outbox,
+                    g->bcast[0],   g->bcast[1],   g->rq,      g->log,        g->sel,        g->snap_value,
+                    g->q[0][0],    g->q[0][1],    g->q[1][0], g->q[1][1],    g->hq[0],      g->hq[1]};
     for (void* p : bufs)
         if (p) cudaFree(p);
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < 5; ++i)
+            if (g->bin_mem[k][i]) cudaFree(g->bin_mem[k][i]);
     if (!g->csc_alias) {
         if (g->csc_off) cudaFree(g->csc_off);
         if (g->csc_row) cudaFree(g->csc_row);

@@ -14,8 +14,9 @@ constexpr int APP_PR = IP_PAGERANK, APP_HM = IP_HASHMIN, APP_SSSP = IP_SSSP;
 constexpr int N_FEATURES = 8;
 constexpr uint32_t MAX_SEQ = 64;
 constexpr int BLOCK = 256;  // threads per CTA for every superstep kernel
-constexpr uint32_t DEFAULT_T1 = 32;
-constexpr uint32_t DEFAULT_T2 = 4096;
+constexpr uint32_t DEFAULT_T1 = 16;
+constexpr uint32_t DEFAULT_T2 = 1024;
+constexpr uint32_t HCH = 4096;  // edges per heavy-vertex chunk (one CTA pass: 256 threads x 4 blocks x 4)
 
 // Device control block: the counters the kernels of one superstep fill, and the
 // decision the selector kernel takes after it. Lives in device memory; the host
@@ -27,9 +28,8 @@ struct DevCtl {
     unsigned long long msgs;  // messages sent = sum of out-degrees of broadcasters
     unsigned int max_deg;   // largest out-degree among broadcasters
     unsigned int rq_len;    // recipient queue length (push-sparse)
-    unsigned int bq_len[2]; // light broadcaster queue lengths, by superstep parity
-    unsigned int hq_len[2]; // heavy broadcaster queue lengths, by superstep parity
-    unsigned int q_valid;   // queue of parity (superstep & 1) holds exactly the bcast bitmap
+    unsigned int q_len[2][3];  // broadcaster queue lengths [superstep parity][small, medium, heavy]
+    unsigned int q_valid;   // the queues of the last completed superstep hold exactly its bcast bitmap
     // decision state (owned by the selector kernel)
     unsigned int superstep; // superstep being computed; at selector time, the one just completed
     unsigned int mode;      // mode of the next exchange
@@ -59,6 +59,21 @@ struct SelectorDev {
 };
 static_assert(sizeof(SelectorDev) == IP_SELECTOR_BYTES, "selector layout");
 
+// Static degree bins of one edge direction (CSR out-edges or CSC in-edges).
+// small: deg <= t1 (handled lane-per-vertex inside 32-vertex tiles);
+// med:   t1 < deg < t2 (warp per vertex);
+// heavy: deg >= t2, split into chunks of at most HCH edges (CTA per chunk).
+struct Bins {
+    const uint32_t* med;
+    uint32_t n_med;
+    uint32_t n_hchunk;
+    const uint4* hchunk;  // {vertex, first edge, end edge, heavy-vertex index}
+    const uint2* hvert;   // per heavy vertex: {first chunk, chunk count}
+    uint32_t n_hvert;
+    uint32_t* hcnt;       // per heavy vertex: chunk arrival counter (PageRank finish), kept at 0 between launches
+    float2* hpart;        // per chunk: compensated partial sum (PageRank)
+};
+
 // Everything a superstep kernel needs, passed by value.
 struct Params {
     uint32_t V;
@@ -70,23 +85,21 @@ struct Params {
     const uint32_t* csc_off;
     const uint32_t* csc_row;
     const uint32_t* csc_w;
-    const uint32_t* heavy_out;  // vertices with out-degree >= t2
-    const uint32_t* heavy_in;   // vertices with in-degree >= t2
-    uint32_t n_heavy_out, n_heavy_in;
+    Bins bout, bin;  // degree bins of the CSR and of the CSC
     const float* inv_outdeg;
     uint32_t* value;
     float* rank;
     float* contrib0;
     float* contrib1;
     uint32_t* mbox;
+    uint32_t* outbox;  // broadcast slot: the value of a vertex that broadcast in the last superstep, else INF
     float* mboxf;
     uint32_t* recv;
-    uint32_t* bcast;
+    uint32_t* bcast0;  // broadcast bitmap of even supersteps
+    uint32_t* bcast1;  // broadcast bitmap of odd supersteps
     uint32_t* rq;
-    uint32_t* bq0;
-    uint32_t* bq1;
-    uint32_t* hq0;
-    uint32_t* hq1;
+    uint32_t* q[2][2];  // broadcaster queues [parity][small, medium]
+    uint2* hq[2];       // heavy broadcaster chunks [parity]: {vertex, chunk index}
     DevCtl* ctl;
     LogRec* log;
     uint32_t log_cap;
@@ -122,21 +135,23 @@ struct ip_graph {
     bool weighted = false;
     uint32_t max_out_deg = 0, max_in_deg = 0;
     float* inv_outdeg = nullptr;
-    uint32_t bins_t2 = 0;
-    uint32_t* heavy_out = nullptr;
-    uint32_t* heavy_in = nullptr;
-    uint32_t n_heavy_out = 0, n_heavy_in = 0;
+    uint32_t bins_t1 = 0, bins_t2 = 0;
+    ipg::Bins bins[2] = {};     // [0] CSR, [1] CSC (aliases [0] for a symmetric graph)
+    void* bin_mem[2][5] = {};  // device buffers behind bins[k]
+    size_t bin_bytes[2][5] = {};
     // run state
     uint32_t* value = nullptr;
     float* rank = nullptr;
     float* contrib[2] = {nullptr, nullptr};
     uint32_t* mbox = nullptr;
+    uint32_t* outbox = nullptr;
     float* mboxf = nullptr;
     uint32_t* recv = nullptr;
-    uint32_t* bcast = nullptr;
+    uint32_t* bcast[2] = {nullptr, nullptr};
     uint32_t* rq = nullptr;
-    uint32_t* bq[2] = {nullptr, nullptr};
-    uint32_t* hq[2] = {nullptr, nullptr};
+    uint32_t* q[2][2] = {};
+    uint2* hq[2] = {nullptr, nullptr};  // capacity: heavy chunks of the CSR (allocated with the bins)
+    uint32_t hq_cap = 0;
     ipg::DevCtl* ctl = nullptr;
     ipg::DevCtl* ctl_host = nullptr;  // pinned mirror
     ipg::LogRec* log = nullptr;
@@ -147,7 +162,7 @@ struct ip_graph {
     uint64_t device_bytes = 0;
     // scratch used by label collection (snapshots)
     uint32_t* snap_value = nullptr;
-    uint32_t* snap_bcast = nullptr;
+
     // cached CUDA graph of the last device-side run
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -161,7 +176,7 @@ struct ip_graph {
 namespace ipg {
 // graph.cu
 int alloc_dev(ip_graph* g, void** p, size_t bytes);
-int ensure_bins(ip_graph* g, uint32_t t2, cudaStream_t st);
+int ensure_bins(ip_graph* g, uint32_t t1, uint32_t t2, cudaStream_t st);
 int cuda_err(cudaError_t e);
 // superstep.cu
 int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* opt, ip_run_stats_t* stats);

@@ -3,26 +3,31 @@
 // One superstep s >= 1 (Section 4.2, Fig. 3) is:
 //   exchange  deliver the messages broadcast in superstep s-1 into the one-slot
 //             mailboxes (Section 4.3.3), in one of three modes (Section 4.3.2):
-//               push-sparse  senders taken from a compacted queue (selection
-//                            bypass, Section 4.3.1); the first message to reach
-//                            a vertex appends it to the recipient queue
+//               push-sparse  senders taken from compacted queues (the selection
+//                            bypass of Section 4.3.1); the first message to
+//                            reach a vertex appends it to the recipient queue
 //               push-dense   senders taken from the broadcast bitmap
 //               pull         every vertex folds its in-neighbours' broadcasts
 //             Push combines with atomicMin (min apps) or atomicAdd (PageRank):
 //             the lock-free combiners that Section 4.3.2 leaves as future work.
 //   apply     compute() of every recipient (Figs. 9, 10) or of every vertex
 //             (PageRank, Fig. 8): read and reset the mailbox, update the value,
-//             decide whether to broadcast, vote to halt; also the frontier
+//             decide whether to broadcast, vote to halt; plus the frontier
 //             statistics of the superstep.
 //   select    one warp: halt test (Section 4.2: every vertex halted and no
 //             message in flight), frontier features, mode of the next exchange
 //             (threshold rule or the learned MLP), per-superstep log.
-// PageRank's pull mode fuses exchange and apply: the broadcast value is held in
-// two buffers (read s-1, write s), so one kernel per superstep suffices.
+// PageRank's pull mode fuses exchange and apply: the broadcast values are held
+// in two buffers (read s-1, write s), so one kernel per superstep suffices.
 //
-// Scheduling (degree bins): a vertex with degree <= t1 is handled by one lane,
-// t1 < degree < t2 by a whole warp, degree >= t2 by a whole CTA. Edge arrays are
-// read as aligned 16-byte blocks.
+// Broadcast bitmaps are double-buffered by superstep parity, as are the
+// broadcaster queues.
+//
+// Scheduling uses static degree bins per edge direction: a vertex with degree
+// <= t1 is handled by one lane inside a 32-vertex tile, t1 < degree < t2 by a
+// whole warp, degree >= t2 in chunks of HCH edges by whole CTAs. Every kernel
+// runs the CTA chunks first, then the warp vertices, then the tiles. Edge
+// arrays are read as aligned 16-byte blocks, U blocks in flight per thread.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -32,6 +37,8 @@
 #include "internal.h"
 
 namespace ipg {
+
+constexpr int U = 4;  // 16-byte blocks loaded per thread before they are consumed
 
 // ----------------------------------------------------------------- helpers
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
@@ -46,7 +53,7 @@ __device__ __forceinline__ uint64_t globaltimer() {
     return t;
 }
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
-    uint32_t s = a + b;
+    const uint32_t s = a + b;
     return s < a ? INF : s;
 }
 __device__ __forceinline__ uint4 ld4(const uint32_t* p, uint32_t blk) {
@@ -60,6 +67,8 @@ __device__ __forceinline__ bool bit_of(const uint32_t* bm, uint32_t v) {
 }
 __device__ __forceinline__ uint32_t global_warp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
 __device__ __forceinline__ uint32_t num_warps() { return (gridDim.x * blockDim.x) >> 5; }
+__device__ __forceinline__ const uint32_t* bc_of(const Params& P, uint32_t s) { return (s & 1) ? P.bcast1 : P.bcast0; }
+__device__ __forceinline__ uint32_t* bc_mut(const Params& P, uint32_t s) { return (s & 1) ? P.bcast1 : P.bcast0; }
 
 // All 32 lanes call; lanes with pred append v to q (one atomic per warp).
 __device__ __forceinline__ void warp_append(bool pred, uint32_t v, uint32_t* q, unsigned int* len) {
@@ -72,13 +81,36 @@ __device__ __forceinline__ void warp_append(bool pred, uint32_t v, uint32_t* q, 
     if (pred) q[base + __popc(m & lanemask_lt())] = v;
 }
 
-// Error-free transformation of a + b (Knuth's TwoSum): s + err == a + b exactly.
+// All 32 lanes call; each lane appends its vertex's HCH-edge chunks {v, c}.
+__device__ __forceinline__ void warp_append_chunks(uint32_t nch, uint32_t v, uint2* q, unsigned int* len) {
+    uint32_t inc = nch;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane_id() >= (uint32_t)o) inc += y;
+    }
+    const uint32_t total = __shfl_sync(FULL, inc, 31);
+    if (!total) return;
+    uint32_t base = 0;
+    if (lane_id() == 31) base = atomicAdd(len, total);
+    base = __shfl_sync(FULL, base, 31) + inc - nch;
+    for (uint32_t c = 0; c < nch; ++c) q[base + c] = make_uint2(v, c);
+}
+
+// Error-free transformation (Knuth's TwoSum): s + err == s_old + x exactly.
 __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
     const float t = s + x;
     const float bp = t - s;
     const float err = (s - (t - bp)) + (x - bp);
     s = t;
     c += err;
+}
+
+__device__ __forceinline__ void warp_two_sum(float& s, float& c) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_down_sync(FULL, s, o), oc = __shfl_down_sync(FULL, c, o);
+        two_sum_acc(s, c, os);
+        c += oc;
+    }
 }
 
 struct Stats {
@@ -115,14 +147,24 @@ __device__ void flush_stats(Stats st, DevCtl* ctl) {
     }
 }
 
+// Appends a broadcaster to the queue of its degree bin (all 32 lanes call).
+__device__ __forceinline__ void queue_broadcaster(const Params& P, int par, bool b, uint32_t v, uint32_t deg) {
+    unsigned int* len = P.ctl->q_len[par];
+    warp_append(b && deg <= P.t1, v, P.q[par][0], &len[0]);
+    warp_append(b && deg > P.t1 && deg < P.t2, v, P.q[par][1], &len[1]);
+    warp_append_chunks(b && deg >= P.t2 ? (deg + HCH - 1) / HCH : 0u, v, P.hq[par], &len[2]);
+}
+
 // =========================================================== superstep 0
-// Hashmin (Fig. 9): value = id, everybody broadcasts. SSSP (Fig. 10): the
-// source takes 0 and broadcasts, everybody else INF.
+// Hashmin (Fig. 9): value = id, every vertex broadcasts. SSSP (Fig. 10): the
+// source takes 0 and broadcasts, every other vertex INF.
 __global__ void k_init_min(Params P) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     const bool hm = P.app == APP_HM;
     for (uint32_t v = tid; v < P.V; v += nth) {
-        P.value[v] = hm ? v : (v == P.source ? 0u : INF);
+        const uint32_t x = hm ? v : (v == P.source ? 0u : INF);
+        P.value[v] = x;
+        P.outbox[v] = x;  // every initial value below INF is broadcast
         P.mbox[v] = INF;
     }
     for (uint32_t w = tid; w < P.W; w += nth) {
@@ -137,7 +179,7 @@ __global__ void k_init_min(Params P) {
         } else if (w == (P.source >> 5)) {
             b = 1u << (P.source & 31u);
         }
-        P.bcast[w] = b;
+        P.bcast0[w] = b;
     }
     if (tid == 0) {
         DevCtl* c = P.ctl;
@@ -149,23 +191,28 @@ __global__ void k_init_min(Params P) {
         c->t_prev = globaltimer();
         c->n_active = P.V;
         c->rq_len = 0;
-        c->bq_len[0] = c->bq_len[1] = 0;
-        c->hq_len[0] = c->hq_len[1] = 0;
+        for (int p = 0; p < 2; ++p)
+            for (int k = 0; k < 3; ++k) c->q_len[p][k] = 0;
         if (hm) {
             c->n_bcast = P.V;
             c->msgs = P.E;
             c->max_deg = P.max_out_deg;
             c->q_valid = 0;
         } else {
+            const uint32_t d = P.out_deg_src;
             c->n_bcast = 1;
-            c->msgs = P.out_deg_src;
-            c->max_deg = P.out_deg_src;
-            if (P.out_deg_src >= P.t2) {
-                P.hq0[0] = P.source;
-                c->hq_len[0] = 1;
+            c->msgs = d;
+            c->max_deg = d;
+            if (d <= P.t1) {
+                P.q[0][0][0] = P.source;
+                c->q_len[0][0] = 1;
+            } else if (d < P.t2) {
+                P.q[0][1][0] = P.source;
+                c->q_len[0][1] = 1;
             } else {
-                P.bq0[0] = P.source;
-                c->bq_len[0] = 1;
+                const uint32_t nch = (d + HCH - 1) / HCH;
+                for (uint32_t k = 0; k < nch; ++k) P.hq[0][k] = make_uint2(P.source, k);
+                c->q_len[0][2] = nch;
             }
             c->q_valid = 1;
         }
@@ -193,253 +240,253 @@ __global__ void k_pr_init(Params P) {
 }
 
 // ============================================================ push (min apps)
-template <int APP, bool SPARSE>
-__device__ __forceinline__ void push_edge(const Params& P, bool live, uint32_t v, uint32_t msg) {
-    bool first = false;
-    if (live) {
-        if (msg < __ldcg(P.mbox + v)) atomicMin(P.mbox + v, msg);
-        const uint32_t bit = 1u << (v & 31u);
-        uint32_t* rw = P.recv + (v >> 5);
-        if (!(__ldcg(rw) & bit)) first = !(atomicOr(rw, bit) & bit);
-    }
-    if (SPARSE) warp_append(first, v, P.rq, &P.ctl->rq_len);
-}
-
 template <int APP>
 __device__ __forceinline__ uint32_t edge_msg(uint32_t val, const uint4& qw, int j) {
     if (APP == APP_HM) return val;
     return sat_add(val, qa(qw, j));
 }
 
-// Edges of the 16-byte block `blk`, restricted to [beg, end), pushed with value val.
-template <int APP, bool SPARSE>
-__device__ __forceinline__ void push_block(const Params& P, bool ok, uint32_t blk, uint32_t beg, uint32_t end,
-                                           uint32_t val) {
-    uint4 qc = make_uint4(0, 0, 0, 0), qw = make_uint4(1, 1, 1, 1);
-    if (ok) {
-        qc = ld4(P.csr_col, blk);
-        if (APP == APP_SSSP && P.csr_w) qw = ld4(P.csr_w, blk);
+// One message into v's mailbox (min combiner) and v's recipient bit. With
+// SPARSE, the first message to reach v appends v to the recipient queue; all
+// 32 lanes must call.
+template <bool SPARSE>
+__device__ __forceinline__ void push_edge(const Params& P, bool live, uint32_t v, uint32_t msg) {
+    bool first = false;
+    if (live) {
+        if (msg < __ldcg(P.mbox + v)) atomicMin(P.mbox + v, msg);
+        const uint32_t bit = 1u << (v & 31u);
+        uint32_t* rw = P.recv + (v >> 5);
+        if (!(__ldcg(rw) & bit)) {
+            if (SPARSE)
+                first = !(atomicOr(rw, bit) & bit);
+            else
+                atomicOr(rw, bit);
+        }
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const uint32_t e = blk * 4 + j;
-        const bool live = ok && e >= beg && e < end;
-        push_edge<APP, SPARSE>(P, live, qa(qc, j), edge_msg<APP>(val, qw, j));
-    }
+    if (SPARSE) warp_append(first, v, P.rq, &P.ctl->rq_len);
 }
 
-// A warp pushes the broadcasts of up to 32 lane-owned senders (degree < t2).
+// Pushes the edges [b, e) of one sender with value val. The thread at position
+// pos of a group of `stride` threads takes 16-byte blocks pos, pos+stride, ...
+// in `trips` iterations of U blocks; with SPARSE, trips must be equal over the warp.
 template <int APP, bool SPARSE>
-__device__ __forceinline__ void push_group(const Params& P, uint32_t u, bool act) {
-    uint32_t beg = 0, end = 0, val = 0;
-    if (act) {
-        beg = P.csr_off[u];
-        end = P.csr_off[u + 1];
-        val = P.value[u];
-    }
-    const uint32_t deg = end - beg;
-    const bool small = act && deg > 0 && deg <= P.t1;
-    const bool med = act && deg > P.t1 && deg < P.t2;
-    // lane-owned senders
-    const uint32_t b0 = beg >> 2;
-    const uint32_t nb = small ? ((end + 3) >> 2) - b0 : 0;
-    const uint32_t maxnb = __reduce_max_sync(FULL, nb);
-    for (uint32_t it = 0; it < maxnb; ++it) push_block<APP, SPARSE>(P, it < nb, b0 + it, beg, end, val);
-    // warp-owned senders
-    uint32_t mm = __ballot_sync(FULL, med);
-    while (mm) {
-        const int l = __ffs(mm) - 1;
-        mm &= mm - 1;
-        const uint32_t mb = __shfl_sync(FULL, beg, l), me = __shfl_sync(FULL, end, l);
-        const uint32_t mv = __shfl_sync(FULL, val, l);
-        const uint32_t bs = mb >> 2, be = (me + 3) >> 2;
-        const uint32_t iters = (be - bs + 31) >> 5;
-        for (uint32_t k = 0; k < iters; ++k) {
-            const uint32_t blk = bs + k * 32 + lane_id();
-            push_block<APP, SPARSE>(P, blk < be, blk, mb, me, mv);
+__device__ __forceinline__ void push_range(const Params& P, uint32_t val, uint32_t b, uint32_t e, uint32_t pos,
+                                           uint32_t stride, uint32_t trips) {
+    const uint32_t bs = b >> 2, be = (e + 3) >> 2;
+    for (uint32_t t = 0; t < trips; ++t) {
+        uint4 qc[U], qw[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t blk = bs + (t * U + u) * stride + pos;
+            const bool ok = blk < be;
+            qc[u] = ok ? ld4(P.csr_col, blk) : make_uint4(0, 0, 0, 0);
+            qw[u] = (APP == APP_SSSP && P.csr_w && ok) ? ld4(P.csr_w, blk) : make_uint4(1, 1, 1, 1);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t blk = bs + (t * U + u) * stride + pos;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t ei = blk * 4 + j;
+                const bool live = blk < be && ei >= b && ei < e;
+                push_edge<SPARSE>(P, live, qa(qc[u], j), edge_msg<APP>(val, qw[u], j));
+            }
         }
     }
 }
 
-// A whole CTA pushes the broadcast of one sender with degree >= t2.
-template <int APP, bool SPARSE>
-__device__ __forceinline__ void push_heavy(const Params& P, uint32_t u) {
-    const uint32_t beg = P.csr_off[u], end = P.csr_off[u + 1], val = P.value[u];
-    const uint32_t bs = beg >> 2, be = (end + 3) >> 2;
-    const uint32_t iters = (be - bs + blockDim.x - 1) / blockDim.x;
-    for (uint32_t k = 0; k < iters; ++k) {
-        const uint32_t blk = bs + k * blockDim.x + threadIdx.x;
-        push_block<APP, SPARSE>(P, blk < be, blk, beg, end, val);
-    }
+__device__ __forceinline__ uint32_t trips_of(uint32_t b, uint32_t e, uint32_t stride) {
+    const uint32_t nb = e > b ? ((e + 3) >> 2) - (b >> 2) : 0u;
+    return (nb + stride * U - 1) / (stride * U);
 }
 
 template <int APP, bool SPARSE>
 __global__ void __launch_bounds__(BLOCK) k_push(Params P) {
-    const uint32_t s = P.ctl->superstep - 1;  // deliver the broadcasts of superstep s
-    const int par = s & 1;
+    const uint32_t sp = P.ctl->superstep - 1;  // deliver the broadcasts of superstep sp
+    const int par = sp & 1;
     if (SPARSE) {
-        const uint32_t nh = P.ctl->hq_len[par];
-        const uint32_t* hq = par ? P.hq1 : P.hq0;
-        for (uint32_t i = blockIdx.x; i < nh; i += gridDim.x) {
-            const uint32_t u = hq[i];
-            if (threadIdx.x == 0) P.bcast[u >> 5] = 0;  // consumed: clear the sender's bitmap word
-            push_heavy<APP, SPARSE>(P, u);
+        // the bitmap of the superstep being computed is built by atomicOr in apply
+        uint32_t* nb = bc_mut(P, sp + 1);
+        for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < P.W; w += gridDim.x * blockDim.x) nb[w] = 0;
+        // heavy senders: one CTA per HCH-edge chunk
+        const uint32_t nh = P.ctl->q_len[par][2];
+        for (uint32_t k = blockIdx.x; k < nh; k += gridDim.x) {
+            const uint2 h = P.hq[par][k];
+            const uint32_t u = h.x, e0 = P.csr_off[u + 1];
+            const uint32_t b = P.csr_off[u] + h.y * HCH, e = min(e0, b + HCH);
+            if (threadIdx.x == 0 && h.y == 0) P.outbox[u] = INF;  // the broadcast slot is consumed
+            push_range<APP, SPARSE>(P, P.value[u], b, e, threadIdx.x, blockDim.x, trips_of(b, e, blockDim.x));
         }
-        const uint32_t n = P.ctl->bq_len[par];
-        const uint32_t* q = par ? P.bq1 : P.bq0;
-        for (uint32_t base = global_warp() * 32; base < n; base += num_warps() * 32) {
+        // medium senders: one warp each
+        const uint32_t nm = P.ctl->q_len[par][1];
+        const uint32_t* qm = P.q[par][1];
+        for (uint32_t i = global_warp(); i < nm; i += num_warps()) {
+            const uint32_t u = qm[i];
+            const uint32_t b = P.csr_off[u], e = P.csr_off[u + 1];
+            if (lane_id() == 0) P.outbox[u] = INF;
+            push_range<APP, SPARSE>(P, P.value[u], b, e, lane_id(), 32, trips_of(b, e, 32));
+        }
+        // small senders: one lane each
+        const uint32_t ns = P.ctl->q_len[par][0];
+        const uint32_t* qs = P.q[par][0];
+        for (uint32_t base = global_warp() * 32; base < ns; base += num_warps() * 32) {
             const uint32_t i = base + lane_id();
-            const bool act = i < n;
-            const uint32_t u = act ? q[i] : 0;
-            if (act) P.bcast[u >> 5] = 0;
-            push_group<APP, SPARSE>(P, u, act);
+            uint32_t b = 0, e = 0, val = 0;
+            if (i < ns) {
+                const uint32_t u = qs[i];
+                b = P.csr_off[u];
+                e = P.csr_off[u + 1];
+                val = P.value[u];
+                P.outbox[u] = INF;
+            }
+            const uint32_t trips = __reduce_max_sync(FULL, trips_of(b, e, 1));
+            push_range<APP, SPARSE>(P, val, b, e, 0, 1, trips);
         }
     } else {
-        for (uint32_t i = blockIdx.x; i < P.n_heavy_out; i += gridDim.x) {
-            const uint32_t u = P.heavy_out[i];
-            if (bit_of(P.bcast, u)) push_heavy<APP, SPARSE>(P, u);
+        const uint32_t* bc = bc_of(P, sp);
+        const Bins& B = P.bout;
+        for (uint32_t k = blockIdx.x; k < B.n_hchunk; k += gridDim.x) {
+            const uint4 ch = B.hchunk[k];
+            if (bit_of(bc, ch.x))
+                push_range<APP, SPARSE>(P, P.value[ch.x], ch.y, ch.z, threadIdx.x, blockDim.x,
+                                        trips_of(ch.y, ch.z, blockDim.x));
         }
-        // 32 bitmap words (1024 vertices) per warp iteration
-        for (uint32_t c = global_warp(); c * 32 < P.W; c += num_warps()) {
-            const uint32_t myw = P.bcast[c * 32 + lane_id()];
-            uint32_t nz = __ballot_sync(FULL, myw != 0);
-            while (nz) {
-                const int j = __ffs(nz) - 1;
-                nz &= nz - 1;
-                const uint32_t word = __shfl_sync(FULL, myw, j);
-                const uint32_t u = (c * 32 + j) * 32 + lane_id();
-                push_group<APP, SPARSE>(P, u, (word >> lane_id()) & 1u);  // heavy lanes skip inside
+        for (uint32_t i = global_warp(); i < B.n_med; i += num_warps()) {
+            const uint32_t u = B.med[i];
+            if (bit_of(bc, u)) {
+                const uint32_t b = P.csr_off[u], e = P.csr_off[u + 1];
+                push_range<APP, SPARSE>(P, P.value[u], b, e, lane_id(), 32, trips_of(b, e, 32));
             }
+        }
+        const uint32_t tiles = (P.V + 31) / 32;
+        for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
+            const uint32_t word = __ldg(bc + t);
+            if (!word) continue;
+            const uint32_t u = t * 32 + lane_id();
+            uint32_t b = 0, e = 0;
+            if ((word >> lane_id()) & 1u) {
+                b = P.csr_off[u];
+                e = P.csr_off[u + 1];
+                if (e - b > P.t1) e = b;  // the warp and CTA bins push these
+            }
+            if (e > b) push_range<APP, SPARSE>(P, P.value[u], b, e, 0, 1, trips_of(b, e, 1));
         }
     }
 }
 
-// Broadcast bitmap -> broadcaster queues of parity (superstep & 1), only when
-// the queues do not already hold the bitmap.
+// Broadcast bitmap of the last completed superstep -> its binned broadcaster
+// queues, unless the queues already hold it.
 __global__ void __launch_bounds__(BLOCK) k_compact(Params P) {
     if (P.ctl->q_valid) return;
-    const uint32_t s = P.ctl->superstep - 1;  // queue the broadcasters of superstep s
-    const int par = s & 1;
-    uint32_t* q = par ? P.bq1 : P.bq0;
-    uint32_t* hq = par ? P.hq1 : P.hq0;
-    unsigned int* ql = &P.ctl->bq_len[par];
-    unsigned int* hl = &P.ctl->hq_len[par];
-    for (uint32_t c = global_warp(); c * 32 < P.W; c += num_warps()) {
-        const uint32_t myw = P.bcast[c * 32 + lane_id()];
-        uint32_t nz = __ballot_sync(FULL, myw != 0);
-        while (nz) {
-            const int j = __ffs(nz) - 1;
-            nz &= nz - 1;
-            const uint32_t word = __shfl_sync(FULL, myw, j);
-            const uint32_t u = (c * 32 + j) * 32 + lane_id();
-            const bool act = (word >> lane_id()) & 1u;
-            const uint32_t deg = act ? P.csr_off[u + 1] - P.csr_off[u] : 0;
-            warp_append(act && deg < P.t2, u, q, ql);
-            warp_append(act && deg >= P.t2, u, hq, hl);
-        }
+    const uint32_t sp = P.ctl->superstep - 1;
+    const int par = sp & 1;
+    const uint32_t* bc = bc_of(P, sp);
+    const uint32_t tiles = (P.V + 31) / 32;
+    for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
+        const uint32_t word = __ldg(bc + t);
+        if (!word) continue;
+        const uint32_t u = t * 32 + lane_id();
+        const bool act = (word >> lane_id()) & 1u;
+        const uint32_t deg = act ? P.csr_off[u + 1] - P.csr_off[u] : 0;
+        queue_broadcaster(P, par, act, u, deg);
     }
 }
 
 // ============================================================ pull (min apps)
-// Folds the in-edges of 16-byte block blk (restricted to [beg,end)) into (m, any).
+// Folds the in-edges [b, e) into (m, any) reading the broadcast slots
+// (outbox[u] = value of u if u broadcast in the last superstep, else INF):
+// the thread at position pos of a group of `stride` threads takes blocks
+// pos, pos+stride, ...
 template <int APP>
-__device__ __forceinline__ void pull_block(const Params& P, uint32_t blk, uint32_t beg, uint32_t end, uint32_t& m,
-                                           bool& any) {
-    const uint4 qr = ld4(P.csc_row, blk);
-    bool hit[4];
-    bool h = false;
+__device__ __forceinline__ void pull_range(const Params& P, uint32_t b, uint32_t e, uint32_t pos, uint32_t stride,
+                                           uint32_t& m, bool& any) {
+    const uint32_t bs = b >> 2, be = (e + 3) >> 2;
+    for (uint32_t g0 = bs + pos; g0 < be; g0 += stride * U) {
+        uint4 qr[U];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const uint32_t e = blk * 4 + j;
-        const uint32_t u = qa(qr, j);
-        hit[j] = e >= beg && e < end && bit_of(P.bcast, u);
-        h |= hit[j];
-    }
-    if (h) {
-        uint4 qw = make_uint4(1, 1, 1, 1);
-        if (APP == APP_SSSP && P.csc_w) qw = ld4(P.csc_w, blk);
+        for (int u = 0; u < U; ++u) {
+            const uint32_t blk = g0 + u * stride;
+            qr[u] = blk < be ? ld4(P.csc_row, blk) : make_uint4(0, 0, 0, 0);
+        }
+        uint32_t x[U][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (hit[j]) {
-                const uint32_t val = __ldg(P.value + qa(qr, j));
-                m = min(m, edge_msg<APP>(val, qw, j));
-                any = true;
+        for (int u = 0; u < U; ++u) {
+            const uint32_t blk = g0 + u * stride;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t ei = blk * 4 + j;
+                x[u][j] = (blk < be && ei >= b && ei < e) ? __ldg(P.outbox + qa(qr[u], j)) : INF;
             }
         }
-    }
-}
-
-template <int APP>
-__device__ __forceinline__ void pull_group(const Params& P, uint32_t tile) {
-    const uint32_t v = tile * 32 + lane_id();
-    const bool valid = v < P.V;
-    uint32_t beg = 0, end = 0;
-    if (valid) {
-        beg = P.csc_off[v];
-        end = P.csc_off[v + 1];
-    }
-    const uint32_t deg = end - beg;
-    const bool small = deg > 0 && deg <= P.t1;
-    const bool med = deg > P.t1 && deg < P.t2;
-    uint32_t m = INF;
-    bool any = false;
-    if (small) {
-        for (uint32_t blk = beg >> 2; blk < ((end + 3) >> 2); ++blk) pull_block<APP>(P, blk, beg, end, m, any);
-    }
-    uint32_t mm = __ballot_sync(FULL, med);
-    while (mm) {
-        const int l = __ffs(mm) - 1;
-        mm &= mm - 1;
-        const uint32_t mb = __shfl_sync(FULL, beg, l), me = __shfl_sync(FULL, end, l);
-        uint32_t pm = INF;
-        bool pa = false;
-        for (uint32_t blk = (mb >> 2) + lane_id(); blk < ((me + 3) >> 2); blk += 32) pull_block<APP>(P, blk, mb, me, pm, pa);
-        pm = __reduce_min_sync(FULL, pm);
-        pa = __any_sync(FULL, pa);
-        if (lane_id() == (uint32_t)l) {
-            m = pm;
-            any = pa;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool h = (x[u][0] & x[u][1] & x[u][2] & x[u][3]) != INF;
+            if (!h) continue;
+            any = true;
+            uint4 qw = make_uint4(1, 1, 1, 1);
+            if (APP == APP_SSSP && P.csc_w) qw = ld4(P.csc_w, g0 + u * stride);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (x[u][j] != INF) m = min(m, edge_msg<APP>(x[u][j], qw, j));
         }
     }
-    if (any) P.mbox[v] = m;
-    const uint32_t bits = __ballot_sync(FULL, any);
-    if (lane_id() == 0 && bits) atomicOr(P.recv + tile, bits);
-}
-
-template <int APP>
-__device__ __forceinline__ void pull_heavy(const Params& P, uint32_t v) {
-    __shared__ uint32_t sm[BLOCK / 32];
-    __shared__ int sa[BLOCK / 32];
-    const uint32_t beg = P.csc_off[v], end = P.csc_off[v + 1];
-    uint32_t m = INF;
-    bool any = false;
-    for (uint32_t blk = (beg >> 2) + threadIdx.x; blk < ((end + 3) >> 2); blk += blockDim.x)
-        pull_block<APP>(P, blk, beg, end, m, any);
-    m = __reduce_min_sync(FULL, m);
-    any = __any_sync(FULL, any);
-    if (lane_id() == 0) {
-        sm[threadIdx.x >> 5] = m;
-        sa[threadIdx.x >> 5] = any;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (uint32_t w = 1; w < blockDim.x / 32; ++w) {
-            m = min(m, sm[w]);
-            any = any || sa[w];
-        }
-        if (any) {
-            P.mbox[v] = m;
-            atomicOr(P.recv + (v >> 5), 1u << (v & 31u));
-        }
-    }
-    __syncthreads();
 }
 
 template <int APP>
 __global__ void __launch_bounds__(BLOCK) k_pull(Params P) {
-    for (uint32_t i = blockIdx.x; i < P.n_heavy_in; i += gridDim.x) pull_heavy<APP>(P, P.heavy_in[i]);
+    __shared__ uint32_t sm[BLOCK / 32];
+    __shared__ uint32_t sa[BLOCK / 32];
+    const Bins& B = P.bin;
+    for (uint32_t k = blockIdx.x; k < B.n_hchunk; k += gridDim.x) {
+        const uint4 ch = B.hchunk[k];
+        uint32_t m = INF;
+        bool any = false;
+        pull_range<APP>(P, ch.y, ch.z, threadIdx.x, blockDim.x, m, any);
+        m = __reduce_min_sync(FULL, m);
+        const uint32_t a = __any_sync(FULL, any);
+        if (lane_id() == 0) {
+            sm[threadIdx.x >> 5] = m;
+            sa[threadIdx.x >> 5] = a;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t mm = INF, aa = 0;
+            for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+                mm = min(mm, sm[w]);
+                aa |= sa[w];
+            }
+            if (aa) {
+                atomicMin(P.mbox + ch.x, mm);
+                atomicOr(P.recv + (ch.x >> 5), 1u << (ch.x & 31u));
+            }
+        }
+        __syncthreads();
+    }
+    for (uint32_t i = global_warp(); i < B.n_med; i += num_warps()) {
+        const uint32_t v = B.med[i];
+        uint32_t m = INF;
+        bool any = false;
+        pull_range<APP>(P, P.csc_off[v], P.csc_off[v + 1], lane_id(), 32, m, any);
+        m = __reduce_min_sync(FULL, m);
+        any = __any_sync(FULL, any);
+        if (lane_id() == 0 && any) {
+            P.mbox[v] = m;
+            atomicOr(P.recv + (v >> 5), 1u << (v & 31u));
+        }
+    }
     const uint32_t tiles = (P.V + 31) / 32;
-    for (uint32_t t = global_warp(); t < tiles; t += num_warps()) pull_group<APP>(P, t);
+    for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
+        const uint32_t v = t * 32 + lane_id();
+        uint32_t m = INF;
+        bool any = false;
+        if (v < P.V) {
+            const uint32_t b = P.csc_off[v], e = P.csc_off[v + 1];
+            if (e - b <= P.t1) pull_range<APP>(P, b, e, 0, 1, m, any);
+        }
+        if (any) P.mbox[v] = m;
+        const uint32_t bits = __ballot_sync(FULL, any);
+        if (lane_id() == 0 && bits) atomicOr(P.recv + t, bits);
+    }
 }
 
 // ============================================================ apply (min apps)
@@ -448,56 +495,53 @@ __device__ __forceinline__ bool apply_vertex(const Params& P, uint32_t v, uint32
     const uint32_t m = P.mbox[v];
     P.mbox[v] = INF;
     const uint32_t val = P.value[v];
+    deg = 0;
     if (m < val) {
         P.value[v] = m;
         deg = P.csr_off[v + 1] - P.csr_off[v];
         return true;  // broadcast the new value
     }
-    deg = 0;
     return false;
 }
 
-// Recipients found in the recv bitmap (after pull or push-dense).
+// Recipients found in the recv bitmap (after pull or push-dense): one warp per
+// 32-vertex word. Writes every word of this superstep's broadcast bitmap and
+// every broadcast slot.
 __global__ void __launch_bounds__(BLOCK) k_apply_bitmap(Params P) {
     Stats st{0, 0, 0, 0};
-    for (uint32_t c = global_warp(); c * 32 < P.W; c += num_warps()) {
-        const uint32_t wi = c * 32 + lane_id();
-        const uint32_t rw = P.recv[wi];
-        if (rw == 0) P.bcast[wi] = 0;
-        uint32_t nz = __ballot_sync(FULL, rw != 0);
-        while (nz) {
-            const int j = __ffs(nz) - 1;
-            nz &= nz - 1;
-            const uint32_t bits = __shfl_sync(FULL, rw, j);
-            const uint32_t wj = c * 32 + j;
-            const uint32_t v = wj * 32 + lane_id();
-            uint32_t deg = 0;
-            const bool b = ((bits >> lane_id()) & 1u) && apply_vertex(P, v, deg);
-            const uint32_t bb = __ballot_sync(FULL, b);
-            if (lane_id() == 0) {
-                P.bcast[wj] = bb;
-                P.recv[wj] = 0;
-                st.act += __popc(bits);
-            }
-            st.bc += b;
-            st.msgs += deg;
-            st.maxd = max(st.maxd, deg);
+    uint32_t* bc = bc_mut(P, P.ctl->superstep);
+    const uint32_t words = (P.V + 31) / 32;
+    for (uint32_t w = global_warp(); w < words; w += num_warps()) {
+        const uint32_t rw = P.recv[w];
+        const uint32_t v = w * 32 + lane_id();
+        uint32_t deg = 0, out = INF;
+        bool b = false;
+        if ((rw >> lane_id()) & 1u) {
+            b = apply_vertex(P, v, deg);
+            if (b) out = P.value[v];
         }
+        if (v < P.V) P.outbox[v] = out;
+        const uint32_t bb = __ballot_sync(FULL, b);
+        if (lane_id() == 0) {
+            bc[w] = bb;
+            if (rw) P.recv[w] = 0;
+            st.act += __popc(rw);
+        }
+        st.bc += b;
+        st.msgs += deg;
+        st.maxd = max(st.maxd, deg);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->q_valid = 0;
     flush_stats(st, P.ctl);
 }
 
 // Recipients taken from the recipient queue (after push-sparse); broadcasters
-// go to the queues of the next parity and to the (cleared) bitmap.
+// go to this superstep's binned queues and (cleared) bitmap.
 __global__ void __launch_bounds__(BLOCK) k_apply_queue(Params P) {
     Stats st{0, 0, 0, 0};
-    const uint32_t s1 = P.ctl->superstep;  // the superstep being computed
-    const int par = s1 & 1;
-    uint32_t* q = par ? P.bq1 : P.bq0;
-    uint32_t* hq = par ? P.hq1 : P.hq0;
-    unsigned int* ql = &P.ctl->bq_len[par];
-    unsigned int* hl = &P.ctl->hq_len[par];
+    const uint32_t s = P.ctl->superstep;
+    const int par = s & 1;
+    uint32_t* bc = bc_mut(P, s);
     const uint32_t n = P.ctl->rq_len;
     for (uint32_t base = global_warp() * 32; base < n; base += num_warps() * 32) {
         const uint32_t i = base + lane_id();
@@ -508,10 +552,12 @@ __global__ void __launch_bounds__(BLOCK) k_apply_queue(Params P) {
             v = P.rq[i];
             P.recv[v >> 5] = 0;  // every bit of this word belongs to a queued recipient
             b = apply_vertex(P, v, deg);
-            if (b) atomicOr(P.bcast + (v >> 5), 1u << (v & 31u));
+            if (b) {
+                atomicOr(bc + (v >> 5), 1u << (v & 31u));
+                P.outbox[v] = P.value[v];
+            }
         }
-        warp_append(b && deg < P.t2, v, q, ql);
-        warp_append(b && deg >= P.t2, v, hq, hl);
+        queue_broadcaster(P, par, b, v, deg);
         st.act += valid;
         st.bc += b;
         st.msgs += deg;
@@ -528,36 +574,48 @@ __device__ __forceinline__ void pr_finish(const Params& P, uint32_t v, float sum
     nxt[v] = s < P.T ? r * P.inv_outdeg[v] : 0.0f;  // broadcast value/out-degree while s < T
 }
 
-__device__ __forceinline__ void pr_pull_block(const uint32_t* row, const float* cur, uint32_t blk, uint32_t beg,
-                                              uint32_t end, float& s, float& c) {
-    const uint4 qr = ld4(row, blk);
+// Compensated sum of cur[u] over the in-edges [b, e); thread pos of a group of
+// `stride` threads takes blocks pos, pos+stride, ...
+__device__ __forceinline__ void pr_gather(const uint32_t* row, const float* cur, uint32_t b, uint32_t e, uint32_t pos,
+                                          uint32_t stride, float& s, float& c) {
+    const uint32_t bs = b >> 2, be = (e + 3) >> 2;
+    for (uint32_t g0 = bs + pos; g0 < be; g0 += stride * U) {
+        uint4 qr[U];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const uint32_t e = blk * 4 + j;
-        if (e >= beg && e < end) two_sum_acc(s, c, __ldg(cur + qa(qr, j)));
-    }
-}
-
-__device__ __forceinline__ void warp_two_sum(float& s, float& c) {
-    for (int o = 16; o > 0; o >>= 1) {
-        const float os = __shfl_down_sync(FULL, s, o), oc = __shfl_down_sync(FULL, c, o);
-        two_sum_acc(s, c, os);
-        c += oc;
+        for (int u = 0; u < U; ++u) {
+            const uint32_t blk = g0 + u * stride;
+            qr[u] = blk < be ? ld4(row, blk) : make_uint4(0, 0, 0, 0);
+        }
+        float x[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t blk = g0 + u * stride;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t ei = blk * 4 + j;
+                x[u][j] = (blk < be && ei >= b && ei < e) ? __ldg(cur + qa(qr[u], j)) : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) two_sum_acc(s, c, x[u][j]);
     }
 }
 
 // Fused exchange + compute for PageRank pull: sum of in-neighbours' broadcasts.
+// A heavy vertex's chunks leave compensated partials; the CTA that completes
+// the last chunk adds them in chunk order and finishes the vertex.
 __global__ void __launch_bounds__(BLOCK) k_pr_pull(Params P) {
     __shared__ float ss[BLOCK / 32], sc[BLOCK / 32];
     const uint32_t s = P.ctl->superstep;  // the superstep being computed
     const float* cur = (s & 1) ? P.contrib0 : P.contrib1;
     float* nxt = (s & 1) ? P.contrib1 : P.contrib0;
-    for (uint32_t i = blockIdx.x; i < P.n_heavy_in; i += gridDim.x) {
-        const uint32_t v = P.heavy_in[i];
-        const uint32_t beg = P.csc_off[v], end = P.csc_off[v + 1];
+    const Bins& B = P.bin;
+    for (uint32_t k = blockIdx.x; k < B.n_hchunk; k += gridDim.x) {
+        const uint4 ch = B.hchunk[k];
         float a = 0.f, c = 0.f;
-        for (uint32_t blk = (beg >> 2) + threadIdx.x; blk < ((end + 3) >> 2); blk += blockDim.x)
-            pr_pull_block(P.csc_row, cur, blk, beg, end, a, c);
+        pr_gather(P.csc_row, cur, ch.y, ch.z, threadIdx.x, blockDim.x, a, c);
         warp_two_sum(a, c);
         if (lane_id() == 0) {
             ss[threadIdx.x >> 5] = a;
@@ -570,90 +628,85 @@ __global__ void __launch_bounds__(BLOCK) k_pr_pull(Params P) {
                 two_sum_acc(ta, tc, ss[w]);
                 tc += sc[w];
             }
-            pr_finish(P, v, ta + tc, s, nxt);
+            B.hpart[k] = make_float2(ta, tc);
+            __threadfence();
+            const uint2 hv = B.hvert[ch.w];
+            if (atomicAdd(B.hcnt + ch.w, 1u) == hv.y - 1) {
+                __threadfence();
+                float fa = 0.f, fc = 0.f;
+                for (uint32_t q = 0; q < hv.y; ++q) {
+                    const float2 pq = __ldcg(B.hpart + hv.x + q);
+                    two_sum_acc(fa, fc, pq.x);
+                    fc += pq.y;
+                }
+                pr_finish(P, ch.x, fa + fc, s, nxt);
+                B.hcnt[ch.w] = 0;
+            }
         }
         __syncthreads();
+    }
+    for (uint32_t i = global_warp(); i < B.n_med; i += num_warps()) {
+        const uint32_t v = B.med[i];
+        float a = 0.f, c = 0.f;
+        pr_gather(P.csc_row, cur, P.csc_off[v], P.csc_off[v + 1], lane_id(), 32, a, c);
+        warp_two_sum(a, c);
+        if (lane_id() == 0) pr_finish(P, v, a + c, s, nxt);
     }
     const uint32_t tiles = (P.V + 31) / 32;
     for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
         const uint32_t v = t * 32 + lane_id();
-        const bool valid = v < P.V;
-        uint32_t beg = 0, end = 0;
-        if (valid) {
-            beg = P.csc_off[v];
-            end = P.csc_off[v + 1];
-        }
-        const uint32_t deg = end - beg;
-        const bool med = deg > P.t1 && deg < P.t2;
-        float a = 0.f, c = 0.f;
-        if (deg <= P.t1) {
-            for (uint32_t blk = beg >> 2; blk < ((end + 3) >> 2); ++blk) pr_pull_block(P.csc_row, cur, blk, beg, end, a, c);
-        }
-        uint32_t mm = __ballot_sync(FULL, med);
-        while (mm) {
-            const int l = __ffs(mm) - 1;
-            mm &= mm - 1;
-            const uint32_t mb = __shfl_sync(FULL, beg, l), me = __shfl_sync(FULL, end, l);
-            float pa = 0.f, pc = 0.f;
-            for (uint32_t blk = (mb >> 2) + lane_id(); blk < ((me + 3) >> 2); blk += 32)
-                pr_pull_block(P.csc_row, cur, blk, mb, me, pa, pc);
-            warp_two_sum(pa, pc);
-            pa = __shfl_sync(FULL, pa, 0);
-            pc = __shfl_sync(FULL, pc, 0);
-            if (lane_id() == (uint32_t)l) {
-                a = pa;
-                c = pc;
+        if (v < P.V) {
+            const uint32_t b = P.csc_off[v], e = P.csc_off[v + 1];
+            if (e - b <= P.t1) {
+                float a = 0.f, c = 0.f;
+                pr_gather(P.csc_row, cur, b, e, 0, 1, a, c);
+                pr_finish(P, v, a + c, s, nxt);
             }
         }
-        if (valid && deg < P.t2) pr_finish(P, v, a + c, s, nxt);
     }
 }
 
 // PageRank push: every vertex adds value/out-degree into its out-neighbours' mailboxes.
-__device__ __forceinline__ void pr_push_block(const Params& P, bool ok, uint32_t blk, uint32_t beg, uint32_t end,
-                                              float x) {
-    if (!ok) return;
-    const uint4 qc = ld4(P.csr_col, blk);
+__device__ __forceinline__ void pr_scatter(const Params& P, float x, uint32_t b, uint32_t e, uint32_t pos,
+                                           uint32_t stride) {
+    const uint32_t bs = b >> 2, be = (e + 3) >> 2;
+    for (uint32_t g0 = bs + pos; g0 < be; g0 += stride * U) {
+        uint4 qc[U];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const uint32_t e = blk * 4 + j;
-        if (e >= beg && e < end) atomicAdd(P.mboxf + qa(qc, j), x);
+        for (int u = 0; u < U; ++u) {
+            const uint32_t blk = g0 + u * stride;
+            qc[u] = blk < be ? ld4(P.csr_col, blk) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t blk = g0 + u * stride;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t ei = blk * 4 + j;
+                if (blk < be && ei >= b && ei < e) atomicAdd(P.mboxf + qa(qc[u], j), x);
+            }
+        }
     }
 }
 
 __global__ void __launch_bounds__(BLOCK) k_pr_push(Params P) {
-    const uint32_t s = P.ctl->superstep - 1;  // deliver the broadcasts of superstep s
-    const float* cur = (s & 1) ? P.contrib1 : P.contrib0;
-    for (uint32_t i = blockIdx.x; i < P.n_heavy_out; i += gridDim.x) {
-        const uint32_t u = P.heavy_out[i];
-        const uint32_t beg = P.csr_off[u], end = P.csr_off[u + 1];
-        const float x = cur[u];
-        for (uint32_t blk = (beg >> 2) + threadIdx.x; blk < ((end + 3) >> 2); blk += blockDim.x)
-            pr_push_block(P, true, blk, beg, end, x);
+    const uint32_t sp = P.ctl->superstep - 1;  // deliver the broadcasts of superstep sp
+    const float* cur = (sp & 1) ? P.contrib1 : P.contrib0;
+    const Bins& B = P.bout;
+    for (uint32_t k = blockIdx.x; k < B.n_hchunk; k += gridDim.x) {
+        const uint4 ch = B.hchunk[k];
+        pr_scatter(P, cur[ch.x], ch.y, ch.z, threadIdx.x, blockDim.x);
+    }
+    for (uint32_t i = global_warp(); i < B.n_med; i += num_warps()) {
+        const uint32_t u = B.med[i];
+        pr_scatter(P, cur[u], P.csr_off[u], P.csr_off[u + 1], lane_id(), 32);
     }
     const uint32_t tiles = (P.V + 31) / 32;
     for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
         const uint32_t u = t * 32 + lane_id();
-        const bool valid = u < P.V;
-        uint32_t beg = 0, end = 0;
-        float x = 0.f;
-        if (valid) {
-            beg = P.csr_off[u];
-            end = P.csr_off[u + 1];
-            x = cur[u];
-        }
-        const uint32_t deg = end - beg;
-        if (deg <= P.t1) {
-            for (uint32_t blk = beg >> 2; blk < ((end + 3) >> 2); ++blk) pr_push_block(P, true, blk, beg, end, x);
-        }
-        uint32_t mm = __ballot_sync(FULL, deg > P.t1 && deg < P.t2);
-        while (mm) {
-            const int l = __ffs(mm) - 1;
-            mm &= mm - 1;
-            const uint32_t mb = __shfl_sync(FULL, beg, l), me = __shfl_sync(FULL, end, l);
-            const float mx = __shfl_sync(FULL, x, l);
-            for (uint32_t blk = (mb >> 2) + lane_id(); blk < ((me + 3) >> 2); blk += 32)
-                pr_push_block(P, true, blk, mb, me, mx);
+        if (u < P.V) {
+            const uint32_t b = P.csr_off[u], e = P.csr_off[u + 1];
+            if (e - b <= P.t1) pr_scatter(P, cur[u], b, e, 0, 1);
         }
     }
 }
@@ -765,8 +818,7 @@ __global__ void k_select(Params P) {
             c->msgs = 0;
             c->max_deg = 0;
             c->rq_len = 0;
-            c->bq_len[s1 & 1] = 0;
-            c->hq_len[s1 & 1] = 0;
+            for (int k = 0; k < 3; ++k) c->q_len[s1 & 1][k] = 0;
         }
         if (P.use_graph) {
             cudaGraphSetConditional(P.h_switch, (unsigned)mode);
@@ -795,48 +847,65 @@ void compute_grids(ip_graph* g) {
     const void* fns[G_COUNT] = {(const void*)k_pr_pull, (const void*)k_pr_push, (const void*)k_push<APP_HM, true>,
                                 (const void*)k_push<APP_SSSP, true>, (const void*)k_push<APP_HM, false>,
                                 (const void*)k_push<APP_SSSP, false>, (const void*)k_pull<APP_HM>,
-                                (const void*)k_pull<APP_SSSP>, nullptr};
-    for (int i = 0; i < G_COUNT; ++i) g->grid[i] = fns[i] ? grid_of(g, fns[i]) : g->num_sms * 4;
+                                (const void*)k_pull<APP_SSSP>, (const void*)k_apply_bitmap};
+    for (int i = 0; i < G_COUNT; ++i) g->grid[i] = grid_of(g, fns[i]);
     g->grids_ready = true;
 }
 
-// Exchange + apply of one superstep in the given mode.
-int launch_superstep(const ip_graph* g, const Params& P, int mode, cudaStream_t st) {
+// Exchange + apply of one superstep in the given mode. With ev (4 events), the
+// boundaries compaction | exchange | apply are recorded on st: ev[0] before the
+// compaction, ev[1] before the exchange, ev[2] before the apply, ev[3] after it.
+int launch_superstep(const ip_graph* g, const Params& P, int mode, cudaStream_t st, cudaEvent_t* ev = nullptr) {
     const int* G = g->grid;
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecord(ev[i], st);
+    };
+    mark(0);
     if (P.app == APP_PR) {
+        mark(1);
         if (mode == IP_MODE_PULL) {
             k_pr_pull<<<G[G_PR_PULL], BLOCK, 0, st>>>(P);
+            mark(2);
         } else {
             k_pr_push<<<G[G_PR_PUSH], BLOCK, 0, st>>>(P);
+            mark(2);
             k_pr_apply<<<G[G_MISC], BLOCK, 0, st>>>(P);
         }
+        mark(3);
         return cuda_err(cudaGetLastError());
     }
     const bool hm = P.app == APP_HM;
     switch (mode) {
         case IP_MODE_PUSH_SPARSE:
             k_compact<<<G[G_MISC], BLOCK, 0, st>>>(P);
+            mark(1);
             if (hm)
                 k_push<APP_HM, true><<<G[G_PUSH_HM_S], BLOCK, 0, st>>>(P);
             else
                 k_push<APP_SSSP, true><<<G[G_PUSH_SSSP_S], BLOCK, 0, st>>>(P);
+            mark(2);
             k_apply_queue<<<G[G_MISC], BLOCK, 0, st>>>(P);
             break;
         case IP_MODE_PUSH_DENSE:
+            mark(1);
             if (hm)
                 k_push<APP_HM, false><<<G[G_PUSH_HM_D], BLOCK, 0, st>>>(P);
             else
                 k_push<APP_SSSP, false><<<G[G_PUSH_SSSP_D], BLOCK, 0, st>>>(P);
+            mark(2);
             k_apply_bitmap<<<G[G_MISC], BLOCK, 0, st>>>(P);
             break;
         default:
+            mark(1);
             if (hm)
                 k_pull<APP_HM><<<G[G_PULL_HM], BLOCK, 0, st>>>(P);
             else
                 k_pull<APP_SSSP><<<G[G_PULL_SSSP], BLOCK, 0, st>>>(P);
+            mark(2);
             k_apply_bitmap<<<G[G_MISC], BLOCK, 0, st>>>(P);
             break;
     }
+    mark(3);
     return cuda_err(cudaGetLastError());
 }
 
@@ -861,24 +930,41 @@ int read_ctl(ip_graph* g, cudaStream_t st) {
     return cuda_err(cudaStreamSynchronize(st));
 }
 
-int host_loop(ip_graph* g, const Params& P, cudaStream_t st) {
-    CKR(launch_init(g, P, st));
-    CKR(read_ctl(g, st));
-    while (!g->ctl_host->done) {
-        CKR(launch_superstep(g, P, (int)g->ctl_host->mode, st));
+// Host-driven superstep loop; with profile, CUDA events time every kernel.
+int host_loop(ip_graph* g, const Params& P, cudaStream_t st, bool profile, ip_run_stats_t* stats) {
+    cudaEvent_t ev[5] = {};
+    if (profile)
+        for (int i = 0; i < 5; ++i) CKR(cuda_err(cudaEventCreate(&ev[i])));
+    int r = launch_init(g, P, st);
+    if (!r) r = read_ctl(g, st);
+    while (!r && !g->ctl_host->done) {
+        const uint32_t s1 = g->ctl_host->superstep;
+        r = launch_superstep(g, P, (int)g->ctl_host->mode, st, profile ? ev : nullptr);
+        if (r) break;
         k_select<<<1, 32, 0, st>>>(P);
-        CKR(cuda_err(cudaGetLastError()));
-        CKR(read_ctl(g, st));
+        if (profile) cudaEventRecord(ev[4], st);
+        r = cuda_err(cudaGetLastError());
+        if (!r) r = read_ctl(g, st);
+        if (!r && profile && stats && stats->kernel_ms && s1 < stats->capacity) {
+            for (int k = 0; k < 4; ++k) {
+                float ms = 0.f;
+                r = cuda_err(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+                if (r) break;
+                stats->kernel_ms[4 * s1 + k] = ms;
+            }
+        }
     }
-    return IP_OK;
+    if (profile)
+        for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+    return r;
 }
 
 // Host loop that, before each exchange, times every mode from the same state.
+// The exchange of superstep s reads the bitmap of s-1 and rewrites that of s,
+// so restoring the values, the broadcast slots and the control block is
+// enough between trials.
 int label_loop(ip_graph* g, const Params& P, cudaStream_t st, ip_run_stats_t* stats) {
-    if (!g->snap_value) {
-        CKR(alloc_dev(g, (void**)&g->snap_value, (size_t)g->V * 4));
-        CKR(alloc_dev(g, (void**)&g->snap_bcast, (size_t)g->W * 4));
-    }
+    if (!g->snap_value) CKR(alloc_dev(g, (void**)&g->snap_value, (size_t)g->V * 8));  // values + broadcast slots
     DevCtl snap_ctl;
     CKR(launch_init(g, P, st));
     CKR(read_ctl(g, st));
@@ -886,22 +972,24 @@ int label_loop(ip_graph* g, const Params& P, cudaStream_t st, ip_run_stats_t* st
         const int chosen = (int)g->ctl_host->mode;
         const uint32_t s1 = g->ctl_host->superstep;  // the superstep about to run
         int order[3], no = 0;
-        const int nmodes = 3;
-        for (int m = 0; m < nmodes; ++m)
+        for (int m = 0; m < 3; ++m)
             if (m != chosen) order[no++] = m;
         order[no++] = chosen;
         snap_ctl = *g->ctl_host;
         if (P.app != APP_PR) {
             CKR(cuda_err(cudaMemcpyAsync(g->snap_value, g->value, (size_t)g->V * 4, cudaMemcpyDeviceToDevice, st)));
-            CKR(cuda_err(cudaMemcpyAsync(g->snap_bcast, g->bcast, (size_t)g->W * 4, cudaMemcpyDeviceToDevice, st)));
+            CKR(cuda_err(cudaMemcpyAsync(g->snap_value + g->V, g->outbox, (size_t)g->V * 4, cudaMemcpyDeviceToDevice,
+                                         st)));
         }
         for (int k = 0; k < no; ++k) {
             const int m = order[k];
             if (k > 0) {  // restore the pre-exchange state
                 CKR(cuda_err(cudaMemcpyAsync(g->ctl, &snap_ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st)));
                 if (P.app != APP_PR) {
-                    CKR(cuda_err(cudaMemcpyAsync(g->value, g->snap_value, (size_t)g->V * 4, cudaMemcpyDeviceToDevice, st)));
-                    CKR(cuda_err(cudaMemcpyAsync(g->bcast, g->snap_bcast, (size_t)g->W * 4, cudaMemcpyDeviceToDevice, st)));
+                    CKR(cuda_err(
+                        cudaMemcpyAsync(g->value, g->snap_value, (size_t)g->V * 4, cudaMemcpyDeviceToDevice, st)));
+                    CKR(cuda_err(cudaMemcpyAsync(g->outbox, g->snap_value + g->V, (size_t)g->V * 4,
+                                                 cudaMemcpyDeviceToDevice, st)));
                 }
             }
             CKR(cuda_err(cudaEventRecord(g->ev0, st)));
@@ -932,7 +1020,7 @@ void free_graph_exec(ip_graph* g) {
 namespace {
 
 // Adds a conditional node at the current capture position of st and makes it the
-// new capture dependency. Returns its body graphs through params.
+// new capture dependency. Returns its body graphs.
 int add_conditional(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, unsigned size,
                     cudaGraph_t** bodies) {
     cudaStreamCaptureStatus cs;
@@ -953,7 +1041,7 @@ int add_conditional(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphCond
 }
 
 // Whole run as one graph: init, select, then while(continue){ switch(mode){...}; select }.
-int build_graph(ip_graph* g, Params P, cudaStream_t st) {
+int build_graph(ip_graph* g, Params P) {
     free_graph_exec(g);
     cudaStream_t cap;
     CKR(cuda_err(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)));
@@ -978,8 +1066,9 @@ int build_graph(ip_graph* g, Params P, cudaStream_t st) {
             break;
         }
         graph = captured;
-        // while body: switch node then select
-        r = cuda_err(cudaStreamBeginCaptureToGraph(cap, wbody[0], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        // while body: switch node, then select
+        r = cuda_err(
+            cudaStreamBeginCaptureToGraph(cap, wbody[0], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         if (r) break;
         cudaGraph_t* sbody = nullptr;
         r = add_conditional(cap, P.h_switch, cudaGraphCondTypeSwitch, 3, &sbody);
@@ -992,7 +1081,8 @@ int build_graph(ip_graph* g, Params P, cudaStream_t st) {
         if (!r) r = cuda_err(e);
         if (r) break;
         for (int m = 0; m < 3 && !r; ++m) {
-            r = cuda_err(cudaStreamBeginCaptureToGraph(cap, sbody[m], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            r = cuda_err(
+                cudaStreamBeginCaptureToGraph(cap, sbody[m], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
             if (r) break;
             r = launch_superstep(g, P, m, cap);
             e = cudaStreamEndCapture(cap, &tmp);
@@ -1033,12 +1123,18 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     const uint32_t t1 = o.t1 ? o.t1 : DEFAULT_T1;
     const uint32_t t2 = o.t2 ? o.t2 : DEFAULT_T2;
     if (t1 >= t2) return IP_E_INVAL;
-    CKR(ensure_bins(g, t2, st));
+    if (g->bins_t1 != t1 || g->bins_t2 != t2) {
+        free_graph_exec(g);
+        CKR(ensure_bins(g, t1, t2, st));
+    }
     compute_grids(g);
 
     const uint32_t want_log = std::min<uint32_t>(max_supersteps, 1u << 16);
     if (g->log_cap < want_log) {
-        if (g->log) cudaFree(g->log);
+        if (g->log) {
+            cudaFree(g->log);
+            g->device_bytes -= (size_t)g->log_cap * sizeof(LogRec);
+        }
         g->log = nullptr;
         g->log_cap = 0;
         CKR(alloc_dev(g, (void**)&g->log, (size_t)want_log * sizeof(LogRec)));
@@ -1057,24 +1153,25 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     P.csc_off = g->csc_off;
     P.csc_row = g->csc_row;
     P.csc_w = g->csc_w;
-    P.heavy_out = g->heavy_out;
-    P.heavy_in = g->heavy_in;
-    P.n_heavy_out = g->n_heavy_out;
-    P.n_heavy_in = g->n_heavy_in;
+    P.bout = g->bins[0];
+    P.bin = g->bins[1];
     P.inv_outdeg = g->inv_outdeg;
     P.value = g->value;
     P.rank = g->rank;
     P.contrib0 = g->contrib[0];
     P.contrib1 = g->contrib[1];
     P.mbox = g->mbox;
+    P.outbox = g->outbox;
     P.mboxf = g->mboxf;
     P.recv = g->recv;
-    P.bcast = g->bcast;
+    P.bcast0 = g->bcast[0];
+    P.bcast1 = g->bcast[1];
     P.rq = g->rq;
-    P.bq0 = g->bq[0];
-    P.bq1 = g->bq[1];
-    P.hq0 = g->hq[0];
-    P.hq1 = g->hq[1];
+    for (int p = 0; p < 2; ++p) {
+        P.q[p][0] = g->q[p][0];
+        P.q[p][1] = g->q[p][1];
+        P.hq[p] = g->hq[p];
+    }
     P.ctl = g->ctl;
     P.log = g->log;
     P.log_cap = g->log_cap;
@@ -1100,10 +1197,12 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
         CKR(cuda_err(cudaStreamSynchronize(st)));
         P.out_deg_src = two[1] - two[0];
     }
-    const bool use_graph = o.use_graph && !o.collect_labels;
+    const bool use_graph = o.use_graph && !o.collect_labels && !o.profile_kernels;
     P.use_graph = use_graph ? 1 : 0;
 
     if (stats && stats->mode_ms && stats->capacity) memset(stats->mode_ms, 0, sizeof(float) * 3 * stats->capacity);
+    if (stats && stats->kernel_ms && stats->capacity)
+        memset(stats->kernel_ms, 0, sizeof(float) * 4 * stats->capacity);
     CKR(cuda_err(cudaEventRecord(g->ev0, st)));
     int r;
     if (o.collect_labels) {
@@ -1113,15 +1212,14 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
         Params key = P;
         key.h_while = key.h_switch = 0;
         if (!g->has_gkey || memcmp(g->gkey, &key, sizeof(Params)) != 0 || !g->gexec) {
-            r = build_graph(g, P, st);
+            r = build_graph(g, P);
             if (r) return r;
             memcpy(g->gkey, &key, sizeof(Params));
             g->has_gkey = true;
         }
         r = cuda_err(cudaGraphLaunch(g->gexec, st));
-        if (!r) r = read_ctl(g, st);
     } else {
-        r = host_loop(g, P, st);
+        r = host_loop(g, P, st, o.profile_kernels != 0, stats);
     }
     if (r) return r;
     CKR(cuda_err(cudaEventRecord(g->ev1, st)));

@@ -240,3 +240,22 @@ def test_full_size_scale22(rmat22s, app):
     with ipg.Graph.from_inputs(g) as G:
         _check_min(G, g, app, ref=ref, policy="threshold")
         _check_min(G, g, app, ref=ref, policy="forced", forced_mode="pull")
+
+
+@pytest.mark.parametrize("app", ["hashmin", "sssp", "pagerank"])
+def test_label_collection_and_kernel_profiling_keep_values(graphs, app):
+    """Timing every mode per superstep (selector training labels) or every kernel
+    leaves the values and the per-superstep counts unchanged."""
+    g = graphs["rmat12s"]
+    with ipg.Graph.from_inputs(g) as G:
+        if app == "pagerank":
+            want, _ = _oracle("pagerank", g)
+            for kw in (dict(collect_labels=1), dict(profile_kernels=1)):
+                st = G.run("pagerank", **kw)
+                assert _pr_err(G.values("pagerank"), want) <= PR_RTOL
+            return
+        ref = _oracle(app, g)
+        st = _check_min(G, g, app, ref=ref, policy="threshold", collect_labels=1)
+        assert (st.mode_ms[1:] > 0).all()
+        st = _check_min(G, g, app, ref=ref, policy="threshold", profile_kernels=1)
+        assert (st.kernel_ms[1:, 1] > 0).all() and (st.kernel_ms[1:, 2] > 0).all()
