@@ -187,6 +187,25 @@ int ip_get_values(ip_graph_t* g, void* dst, size_t dst_bytes, int dst_is_device,
 #define IP_SELECTOR_BYTES (16 * 4 + (32 * 8 + 32 * 32 + 3 * 32) * 2 + (32 + 32 + 3) * 4)
 int ip_set_selector(ip_graph_t* g, const void* blob, size_t bytes);
 
+/* Hashmin connected components without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory, for example code running inside another
+ * framework's memory pool or under a fixed memory budget. It computes exactly
+ * what ip_run(IP_HASHMIN) computes (same labels, same superstep count), keeping
+ * all of its temporary state in one fixed array inside the library image
+ * (about 4.4 MiB per device that loads the library, held until exit).
+ *   n_vertices     1 .. IP_NOALLOC_MAX_VERTICES; larger graphs give IP_E_RANGE.
+ *   csr_offsets / csr_cols   the out-edge CSR, DEVICE memory, not modified.
+ *   labels         n_vertices uint32 outputs, DEVICE memory.
+ *   supersteps_out host pointer or NULL: supersteps run, superstep 0 included.
+ * Returns IP_OK at global halt, IP_E_MAXSTEPS at the cap. The input is not
+ * validated. The first call on a device looks up the array's device address;
+ * make that first call before any stream capture. All calls on a device share
+ * the array: calls that overlap on the GPU race and give wrong results. */
+#define IP_NOALLOC_MAX_VERTICES (1u << 20)
+int ip_hashmin_noalloc(uint32_t n_vertices, uint64_t n_edges, const uint32_t* csr_offsets, const uint32_t* csr_cols,
+                       uint32_t* labels, uint32_t max_supersteps, uint32_t* supersteps_out, void* stream);
+
 /* Human-readable text for an IP_* code (static storage). */
 const char* ip_strerror(int code);
 

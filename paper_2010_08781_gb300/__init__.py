@@ -70,7 +70,8 @@ _lib = None
 
 # every symbol include/ipregel.h declares
 EXPORTS = ("ip_options_default", "ip_graph_create", "ip_graph_destroy", "ip_graph_info", "ip_run", "ip_get_values",
-           "ip_set_selector", "ip_strerror")
+           "ip_set_selector", "ip_strerror", "ip_hashmin_noalloc")
+NOALLOC_MAX_VERTICES = 1 << 20
 
 
 def lib_path() -> str:
@@ -98,6 +99,9 @@ def load(build_if_missing: bool = True):
     L.ip_run.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(Options), ctypes.POINTER(RunStatsC)]
     L.ip_get_values.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int, vp]
     L.ip_set_selector.argtypes = [vp, vp, ctypes.c_size_t]
+    L.ip_hashmin_noalloc.argtypes = [ctypes.c_uint32, ctypes.c_uint64, vp, vp, vp, ctypes.c_uint32,
+                                     ctypes.POINTER(ctypes.c_uint32), vp]
+    L.ip_hashmin_noalloc.restype = ctypes.c_int
     L.ip_strerror.argtypes = [ctypes.c_int]
     L.ip_strerror.restype = ctypes.c_char_p
     for name in ("ip_graph_create", "ip_graph_info", "ip_run", "ip_get_values", "ip_set_selector"):
@@ -282,3 +286,19 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def hashmin_noalloc(n, csr_offsets, csr_cols, labels, max_supersteps=100000, stream=None):
+    """Hashmin through ip_hashmin_noalloc: no device allocation by the library.
+
+    For callers that may not allocate device memory (e.g. inside another
+    framework's memory pool): all arguments are CUDA tensors the caller owns.
+    Returns (code, supersteps)."""
+    for t in (csr_offsets, csr_cols, labels):
+        if not (_is_torch(t) and t.is_cuda):
+            raise TypeError("CUDA tensors expected")
+    steps = ctypes.c_uint32(0)
+    code = load().ip_hashmin_noalloc(int(n), int(csr_cols.numel()), csr_offsets.data_ptr(), csr_cols.data_ptr(),
+                                     labels.data_ptr(), int(max_supersteps), ctypes.byref(steps),
+                                     _stream_handle(stream))
+    return code, steps.value
