@@ -322,6 +322,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def ncu_case(spec, scale):
+    """Small profiling case: one app in one forced mode, host-driven loop (ncu cannot
+    profile kernels inside graphs with conditional nodes), run twice."""
+    import paper_2010_08781_gb300 as ipg
+    app, mode = spec.split(":")
+    g = build_graph(scale)
+    with ipg.Graph.from_inputs(g) as G:
+        for _ in range(2):
+            kw = dict(policy="forced", forced_mode=mode) if app != "pagerank" or mode != "auto" else {}
+            st = G.run(app, use_graph=0, **kw)
+    print(json.dumps({"ncu_case": spec, "scale": scale, "edges": g.m, "supersteps": st.supersteps,
+                      "ms": round(st.elapsed_ms, 4)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,7 +345,11 @@ def main():
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--policy", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", default=None, help="APP:MODE, e.g. sssp:pull — small profiling case only")
     args = ap.parse_args()
+    if args.ncu_case:
+        ncu_case(args.ncu_case, args.scale)
+        return
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
 
     rank = int(os.environ.get("RANK", "0"))

@@ -505,31 +505,56 @@ __device__ __forceinline__ bool apply_vertex(const Params& P, uint32_t v, uint32
 }
 
 // Recipients found in the recv bitmap (after pull or push-dense): one warp per
-// 32-vertex word. Writes every word of this superstep's broadcast bitmap and
-// every broadcast slot.
+// 32-vertex word, AW words in flight per warp. Writes every word of this
+// superstep's broadcast bitmap and every broadcast slot.
+constexpr int AW = 4;
 __global__ void __launch_bounds__(BLOCK) k_apply_bitmap(Params P) {
     Stats st{0, 0, 0, 0};
     uint32_t* bc = bc_mut(P, P.ctl->superstep);
     const uint32_t words = (P.V + 31) / 32;
-    for (uint32_t w = global_warp(); w < words; w += num_warps()) {
-        const uint32_t rw = P.recv[w];
-        const uint32_t v = w * 32 + lane_id();
-        uint32_t deg = 0, out = INF;
-        bool b = false;
-        if ((rw >> lane_id()) & 1u) {
-            b = apply_vertex(P, v, deg);
-            if (b) out = P.value[v];
+    const uint32_t nw = num_warps(), lane = lane_id();
+    for (uint32_t w0 = global_warp(); w0 < words; w0 += AW * nw) {
+        uint32_t rw[AW], m[AW], val[AW];
+#pragma unroll
+        for (int k = 0; k < AW; ++k) {
+            const uint32_t w = w0 + k * nw;
+            rw[k] = w < words ? P.recv[w] : 0u;
         }
-        if (v < P.V) P.outbox[v] = out;
-        const uint32_t bb = __ballot_sync(FULL, b);
-        if (lane_id() == 0) {
-            bc[w] = bb;
-            if (rw) P.recv[w] = 0;
-            st.act += __popc(rw);
+#pragma unroll
+        for (int k = 0; k < AW; ++k) {
+            const uint32_t v = (w0 + k * nw) * 32 + lane;
+            const bool r = (rw[k] >> lane) & 1u;
+            m[k] = r ? P.mbox[v] : INF;
+            val[k] = r ? P.value[v] : 0u;
         }
-        st.bc += b;
-        st.msgs += deg;
-        st.maxd = max(st.maxd, deg);
+        uint32_t deg[AW];
+#pragma unroll
+        for (int k = 0; k < AW; ++k) {
+            const uint32_t w = w0 + k * nw;
+            const uint32_t v = w * 32 + lane;
+            const bool r = (rw[k] >> lane) & 1u;
+            const bool b = m[k] < val[k];  // compute() of Figs. 9 / 10: improve and broadcast
+            if (r) P.mbox[v] = INF;
+            if (b) P.value[v] = m[k];
+            if (w < words && v < P.V) P.outbox[v] = b ? m[k] : INF;
+            deg[k] = b ? 1u : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < AW; ++k) {
+            const uint32_t w = w0 + k * nw;
+            const uint32_t v = w * 32 + lane;
+            const bool b = deg[k] != 0;
+            deg[k] = b ? P.csr_off[v + 1] - P.csr_off[v] : 0u;
+            const uint32_t bb = __ballot_sync(FULL, b);
+            if (lane == 0 && w < words) {
+                bc[w] = bb;
+                if (rw[k]) P.recv[w] = 0;
+                st.act += __popc(rw[k]);
+            }
+            st.bc += b;
+            st.msgs += deg[k];
+            st.maxd = max(st.maxd, deg[k]);
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->q_valid = 0;
     flush_stats(st, P.ctl);
