@@ -187,6 +187,34 @@ int ip_get_values(ip_graph_t* g, void* dst, size_t dst_bytes, int dst_is_device,
 #define IP_SELECTOR_BYTES (16 * 4 + (32 * 8 + 32 * 32 + 3 * 32) * 2 + (32 + 32 + 3) * 4)
 int ip_set_selector(ip_graph_t* g, const void* blob, size_t bytes);
 
+/* ---------------------------------------------------------- selector training
+ * Kernels that train the learned mode selector (not in the paper: the paper
+ * chooses push or pull with a compile flag, Section 4.3.2). The network is the
+ * 8-32-32-3 MLP loaded by ip_set_selector:
+ *   xn = (x - mu)/sd, h1 = relu(W1 xn + b1), h2 = relu(W2 h1 + b2), z = W3 h2 + b3,
+ * loss = sum_i w_i (logsumexp(z_i) - z_i[y_i]) / weight_total.
+ * params: IP_MLP_PARAMS FP32 masters in the order W1[32][8], b1[32], W2[32][32],
+ * b2[32], W3[3][32], b3[3] (row-major, output-major); the weights are rounded to
+ * BF16 (nearest even) inside every pass, accumulation is FP32, and gradients
+ * flow to the FP32 masters. mu_sd: mu[8] then sd[8]. X: n x 8 features, y: n
+ * labels in {0,1,2}, w: n sample weights. All pointers are DEVICE memory; the
+ * caller owns every buffer, including the workspace of the backward pass
+ * (ip_mlp_workspace_bytes() bytes). Gradients are summed in a fixed order:
+ * repeated calls give identical results. */
+#define IP_MLP_PARAMS (32 * 8 + 32 + 32 * 32 + 32 + 3 * 32 + 3)
+size_t ip_mlp_workspace_bytes(void);
+/* logits: n x 3 FP32 outputs. */
+int ip_mlp_forward(const float* params, const float* mu_sd, const float* X, uint32_t n, float* logits, void* stream);
+/* grad: IP_MLP_PARAMS FP32 outputs; loss: one FP32 output (may be NULL). */
+int ip_mlp_backward(const float* params, const float* mu_sd, const float* X, const int32_t* y, const float* w,
+                    uint32_t n, float weight_total, float* grad, float* loss, void* workspace,
+                    size_t workspace_bytes, void* stream);
+/* One Adam step on `count` parameters (step >= 1; bias-corrected). */
+int ip_mlp_adam(float* params, const float* grad, float* m, float* v, uint32_t count, float lr, float beta1,
+                float beta2, float eps, uint32_t step, void* stream);
+/* Writes the IP_SELECTOR_BYTES selector blob (device memory) from the FP32 masters. */
+int ip_mlp_pack(const float* params, const float* mu_sd, void* blob, void* stream);
+
 /* Hashmin connected components without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that may
  * not allocate device memory, for example code running inside another

@@ -70,7 +70,9 @@ _lib = None
 
 # every symbol include/ipregel.h declares
 EXPORTS = ("ip_options_default", "ip_graph_create", "ip_graph_destroy", "ip_graph_info", "ip_run", "ip_get_values",
-           "ip_set_selector", "ip_strerror", "ip_hashmin_noalloc")
+           "ip_set_selector", "ip_strerror", "ip_hashmin_noalloc", "ip_mlp_workspace_bytes", "ip_mlp_forward",
+           "ip_mlp_backward", "ip_mlp_adam", "ip_mlp_pack")
+MLP_PARAMS = 32 * 8 + 32 + 32 * 32 + 32 + 3 * 32 + 3
 NOALLOC_MAX_VERTICES = 1 << 20
 
 
@@ -102,6 +104,16 @@ def load(build_if_missing: bool = True):
     L.ip_hashmin_noalloc.argtypes = [ctypes.c_uint32, ctypes.c_uint64, vp, vp, vp, ctypes.c_uint32,
                                      ctypes.POINTER(ctypes.c_uint32), vp]
     L.ip_hashmin_noalloc.restype = ctypes.c_int
+    L.ip_mlp_workspace_bytes.argtypes = []
+    L.ip_mlp_workspace_bytes.restype = ctypes.c_size_t
+    L.ip_mlp_forward.argtypes = [vp, vp, vp, ctypes.c_uint32, vp, vp]
+    L.ip_mlp_backward.argtypes = [vp, vp, vp, vp, vp, ctypes.c_uint32, ctypes.c_float, vp, vp, vp, ctypes.c_size_t,
+                                  vp]
+    L.ip_mlp_adam.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_uint32, vp]
+    L.ip_mlp_pack.argtypes = [vp, vp, vp, vp]
+    for name in ("ip_mlp_forward", "ip_mlp_backward", "ip_mlp_adam", "ip_mlp_pack"):
+        getattr(L, name).restype = ctypes.c_int
     L.ip_strerror.argtypes = [ctypes.c_int]
     L.ip_strerror.restype = ctypes.c_char_p
     for name in ("ip_graph_create", "ip_graph_info", "ip_run", "ip_get_values", "ip_set_selector"):
@@ -183,7 +195,9 @@ class Graph:
     """A graph resident on the current CUDA device (owns its device memory)."""
 
     def __init__(self, n, csr_offsets, csr_cols, csr_weights=None, csc_offsets=None, csc_rows=None,
-                 csc_weights=None, symmetric=False, stream=None):
+                 csc_weights=None, symmetric=False, stream=None, selector="default"):
+        """selector: "default" loads the trained selector shipped with the package
+        (if present), None loads nothing, bytes load that blob."""
         L = load()
         self._h = ctypes.c_void_p()
         arrays = [csr_offsets, csr_cols, csr_weights, csc_offsets, csc_rows, csc_weights]
@@ -200,17 +214,21 @@ class Graph:
         self.m = m
         st = _stream_handle(stream)
         _check(L.ip_graph_create(ctypes.byref(self._h), self.n, m, *p, device_ptrs, st), "ip_graph_create")
-        self._keep = [x[2] for x in ptrs]
         self._keep = None  # the library copied everything
+        if selector == "default":
+            from .selector import load_default_blob
+            selector = load_default_blob()
+        if selector is not None:
+            self.set_selector(selector)
 
     @classmethod
-    def from_inputs(cls, g, stream=None, build_csc_on_device=False):
+    def from_inputs(cls, g, stream=None, build_csc_on_device=False, selector="default"):
         """From an inputs.Graph (host numpy arrays)."""
         if g.symmetric:
-            return cls(g.n, g.row_ptr, g.col, g.w, symmetric=True, stream=stream)
+            return cls(g.n, g.row_ptr, g.col, g.w, symmetric=True, stream=stream, selector=selector)
         if build_csc_on_device:
-            return cls(g.n, g.row_ptr, g.col, g.w, stream=stream)
-        return cls(g.n, g.row_ptr, g.col, g.w, g.t_ptr, g.t_idx, g.wt, stream=stream)
+            return cls(g.n, g.row_ptr, g.col, g.w, stream=stream, selector=selector)
+        return cls(g.n, g.row_ptr, g.col, g.w, g.t_ptr, g.t_idx, g.wt, stream=stream, selector=selector)
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

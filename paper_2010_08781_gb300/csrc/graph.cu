@@ -415,8 +415,8 @@ void ip_options_default(ip_options_t* o) {
     o->forced_mode = IP_MODE_PULL;
     o->t1 = 0;
     o->t2 = 0;
-    o->thr_sparse = 0.02f;
-    o->thr_pull = 0.15f;
+    o->thr_sparse = 0.00794f;  // cutoffs fitted on measured per-mode superstep times (selector_report.json)
+    o->thr_pull = 0.1122f;
     o->use_graph = 1;
     o->collect_labels = 0;
     o->stream = nullptr;

@@ -775,6 +775,10 @@ __device__ int mlp_mode(const SelectorDev* S, const float* f) {
     return best;
 }
 
+// Restarts the clock of the "last superstep time" feature (label collection:
+// only the final, kept trial of a superstep is timed into the feature).
+__global__ void k_stamp(DevCtl* c) { c->t_prev = globaltimer(); }
+
 __global__ void k_select(Params P) {
     DevCtl* c = P.ctl;
     const uint32_t s = c->superstep;
@@ -1017,6 +1021,7 @@ int label_loop(ip_graph* g, const Params& P, cudaStream_t st, ip_run_stats_t* st
                                                  cudaMemcpyDeviceToDevice, st)));
                 }
             }
+            if (k == no - 1) k_stamp<<<1, 1, 0, st>>>(g->ctl);
             CKR(cuda_err(cudaEventRecord(g->ev0, st)));
             CKR(launch_superstep(g, P, m, st));
             CKR(cuda_err(cudaEventRecord(g->ev1, st)));

@@ -102,7 +102,8 @@ def test_threshold_policy_and_host_loop(graphs, app):
             st = _check_min(G, g, app, ref=ref, policy="threshold", use_graph=use_graph)
             # the threshold rule is a function of the logged feature f6 = msgs / E
             f6 = st.features[:-1, 6]
-            want = np.where(f6 < np.float32(0.02), 0, np.where(f6 >= np.float32(0.15), 2, 1))
+            o = ipg.default_options()
+            want = np.where(f6 < np.float32(o.thr_sparse), 0, np.where(f6 >= np.float32(o.thr_pull), 2, 1))
             assert st.mode[1:].tolist() == want.tolist()
 
 
@@ -156,7 +157,7 @@ def test_edge_cases():
 
 def test_superstep_cap_and_errors(graphs):
     g = inputs.path(50)
-    with ipg.Graph.from_inputs(g) as G:
+    with ipg.Graph.from_inputs(g, selector=None) as G:
         st = G.run("hashmin", max_supersteps=5)
         assert st.code == ipg.IP_E_MAXSTEPS and st.supersteps == 5 and not st.halted
         ref, _ = oracle.hashmin(g.n, g.row_ptr, g.col, max_supersteps=5)

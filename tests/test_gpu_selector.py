@@ -1,0 +1,162 @@
+"""Selector MLP kernels against the FP64 oracle (oracle/mlp.py), and consistency
+between the training forward pass and the inference inside the superstep engine."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import mlp as omlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2010_08781_gb300 as ipg  # noqa: E402
+from paper_2010_08781_gb300 import selector  # noqa: E402
+
+ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def _blob_params(blob):
+    """Parse the selector blob: mu, sd and the BF16-rounded weights as float64."""
+    b = np.frombuffer(blob, dtype=np.uint8)
+    o = 0
+
+    def take(dtype, count):
+        nonlocal o
+        nb = np.dtype(dtype).itemsize * count
+        a = b[o:o + nb].view(dtype)
+        o += nb
+        return a
+
+    mu, sd = take(np.float32, 8), take(np.float32, 8)
+    w = {}
+    for name, shape in (("W1", (32, 8)), ("W2", (32, 32)), ("W3", (3, 32))):
+        h = take(np.uint16, shape[0] * shape[1]).astype(np.uint32) << 16
+        w[name] = h.view(np.float32).astype(np.float64).reshape(shape)
+    w["b1"], w["b2"], w["b3"] = (take(np.float32, k).astype(np.float64) for k in (32, 32, 3))
+    assert o == ipg.SELECTOR_BYTES
+    return mu, sd, w
+
+
+def _trainer_with(seed, X):
+    mu, sd = selector.normalisation(X)
+    return selector.Trainer(mu, sd, seed=seed), mu, sd
+
+
+def _data(seed, n):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(3.0, 2.0, (n, 8)).astype(np.float32)
+    y = rng.integers(0, 3, n).astype(np.int32)
+    w = rng.uniform(0.1, 2.0, n).astype(np.float32)
+    return X, y, w
+
+
+@pytest.mark.parametrize("n", [1, 777, 5000])
+def test_forward_and_gradients_match_fp64_oracle(n):
+    X, y, w = _data(n, n)
+    tr, mu, sd = _trainer_with(n, X)
+    # perturb the biases so every parameter has a non-trivial gradient
+    tr.p += torch.randn_like(tr.p) * 0.05
+    _, _, W = _blob_params(tr.blob())
+    mu64, sd64 = mu.astype(np.float64), sd.astype(np.float64)
+    z_ref, _ = omlp.forward(W, X.astype(np.float64), mu64, sd64)
+    z = tr.logits(X)
+    assert np.max(np.abs(z - z_ref)) <= 1e-4 * max(1.0, np.max(np.abs(z_ref)))
+    Xd, yd, wd = (torch.from_numpy(a).cuda() for a in (X, y, w))
+    g, loss = tr.gradient(Xd, yd, wd, n, float(w.sum()))
+    L_ref, g_ref = omlp.backward(W, X.astype(np.float64), y, w.astype(np.float64), mu64, sd64)
+    assert abs(loss.item() - L_ref) <= 1e-4 * max(1.0, abs(L_ref))
+    g = g.cpu().numpy().astype(np.float64)
+    o = 0
+    for k in ORDER:
+        size = omlp.SHAPES[k][0] * (omlp.SHAPES[k][1] if len(omlp.SHAPES[k]) > 1 else 1)
+        gk = g[o:o + size].reshape(omlp.SHAPES[k])
+        o += size
+        scale = max(np.max(np.abs(g_ref[k])), 1e-6)
+        assert np.max(np.abs(gk - g_ref[k])) <= 1e-3 * scale, k
+    assert o == ipg.MLP_PARAMS
+
+
+def test_gradients_are_deterministic():
+    X, y, w = _data(3, 3000)
+    tr, _, _ = _trainer_with(3, X)
+    Xd, yd, wd = (torch.from_numpy(a).cuda() for a in (X, y, w))
+    g1 = tr.gradient(Xd, yd, wd, 3000, float(w.sum()))[0].clone()
+    g2 = tr.gradient(Xd, yd, wd, 3000, float(w.sum()))[0].clone()
+    assert torch.equal(g1, g2)
+
+
+def test_adam_step_formula():
+    tr, _, _ = _trainer_with(0, _data(0, 10)[0])
+    p0 = tr.p.clone()
+    g = torch.linspace(-1, 1, ipg.MLP_PARAMS, device="cuda")
+    m = torch.zeros_like(p0)
+    v = torch.zeros_like(p0)
+    L = ipg.load()
+    rc = L.ip_mlp_adam(ctypes.c_void_p(tr.p.data_ptr()), ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(m.data_ptr()),
+                       ctypes.c_void_p(v.data_ptr()), ipg.MLP_PARAMS, ctypes.c_float(0.01), ctypes.c_float(0.9),
+                       ctypes.c_float(0.999), ctypes.c_float(1e-8), 1, None)
+    assert rc == 0
+    # first bias-corrected step: p -= lr * g / (|g| + eps)
+    want = p0 - 0.01 * g / (g.abs() + 1e-8)
+    assert torch.allclose(tr.p, want, atol=1e-6)
+
+
+def test_training_learns_a_separable_rule():
+    rng = np.random.default_rng(5)
+    X = rng.normal(0, 1, (4000, 8)).astype(np.float32)
+    y = np.where(X[:, 6] < -0.5, 0, np.where(X[:, 6] > 0.5, 2, 1)).astype(np.int32)
+    w = np.ones(4000, np.float32)
+    tr, _, _ = _trainer_with(1, X)
+    hist = tr.fit(X, y, w, steps=1500, lr=1e-2)
+    acc = (tr.logits(X).argmax(axis=1) == y).mean()
+    assert hist[-1] < hist[0] and acc > 0.95
+
+
+def test_engine_inference_equals_training_forward():
+    """The selector inside the superstep engine picks argmax of the same logits."""
+    g = inputs.rmat_graph(14, symmetrize=True, weighted=True, seed=9)
+    rng = np.random.default_rng(2)
+    X = rng.normal(5.0, 3.0, (256, 8)).astype(np.float32)
+    tr, _, _ = _trainer_with(7, X)
+    tr.p += torch.randn_like(tr.p) * 0.3
+    blob = tr.blob()
+    with ipg.Graph.from_inputs(g) as G:
+        G.set_selector(blob)
+        for app in ("hashmin", "sssp"):
+            st = G.run(app, policy="mlp")
+            feats = st.features[: st.supersteps - 1]
+            want = tr.logits(feats).argmax(axis=1)
+            assert st.mode[1:].tolist() == want.tolist()
+
+
+def test_trained_selector_gain_on_held_out_graph():
+    """What the trained network gains over the fixed threshold rule on a graph it
+    never saw (R-MAT scale 22, seed 41): every superstep times all three modes from
+    the same state; each policy is charged the measured time of the mode it picks."""
+    blob = selector.load_default_blob()
+    assert blob is not None, "trained selector weights missing from the package"
+    g = inputs.rmat_graph(22, symmetrize=True, weighted=True, seed=41)
+    o = ipg.default_options()
+    tot = {"mlp": 0.0, "threshold": 0.0, "best": 0.0, "pull": 0.0}
+    with ipg.Graph.from_inputs(g, selector=blob) as G:
+        for app, src in (("hashmin", 0), ("sssp", 0), ("sssp", 12345)):
+            kw = dict(source=src) if app == "sssp" else {}
+            st = G.run(app, policy="mlp", collect_labels=1, **kw)
+            T = st.mode_ms[1:st.supersteps].astype(np.float64)
+            X = st.features[:st.supersteps - 1]
+            mlp_modes = st.mode[1:st.supersteps].astype(np.int64)
+            thr_modes = selector.threshold_modes(X, o.thr_sparse, o.thr_pull)
+            tot["mlp"] += selector.total_time(mlp_modes, T)
+            tot["threshold"] += selector.total_time(thr_modes, T)
+            tot["best"] += float(T.min(axis=1).sum())
+            tot["pull"] += float(T[:, 2].sum())
+    gain = tot["threshold"] / tot["mlp"] - 1.0
+    print(f"\nselector on held-out R-MAT 22: mlp {tot['mlp']:.3f} ms, threshold {tot['threshold']:.3f} ms, "
+          f"best {tot['best']:.3f} ms, always-pull {tot['pull']:.3f} ms, gain over threshold {100 * gain:+.2f}%")
+    assert tot["mlp"] <= 1.03 * tot["threshold"]  # measured times carry a few percent of noise
+    assert tot["mlp"] < tot["pull"]
