@@ -216,6 +216,24 @@ def report(name, X, T, modes_by_policy):
     return out
 
 
+def live_compare(specs, blob, thr_sparse, thr_pull, reps=5):
+    """Whole runs in the device-driven loop: median ms per policy, per app."""
+    out = []
+    for spec in specs:
+        g = make_graph(spec)
+        with Graph.from_inputs(g, selector=blob) as G:
+            for app in ("hashmin", "sssp"):
+                row = dict(spec, app=app)
+                for name, kw in (("mlp", dict(policy="mlp")),
+                                 ("threshold_tuned", dict(policy="threshold", thr_sparse=thr_sparse,
+                                                          thr_pull=thr_pull)),
+                                 ("pull", dict(policy="forced", forced_mode="pull"))):
+                    ts = sorted(G.run(app, **kw).elapsed_ms for _ in range(reps))
+                    row[name + "_ms"] = round(ts[len(ts) // 2], 4)
+                out.append(row)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("cmd", choices=["train"])
@@ -253,10 +271,11 @@ def main():
                                           "threshold_tuned": threshold_modes(Xev, thr_sparse, thr_pull)}),
         "eval_accuracy": float((pred_ev == labels_of(Tev)[0]).mean()),
     }
+    rep["live_eval"] = live_compare(evaluation_graphs(), blob, thr_sparse, thr_pull)
     with open(os.path.join(args.out, "selector_report.json"), "w") as f:
         json.dump(rep, f, indent=1)
     print(json.dumps({k: rep[k] for k in ("tuned_threshold", "train", "eval", "train_accuracy", "eval_accuracy",
-                                          "train_seconds")}))
+                                          "train_seconds", "live_eval")}))
 
 
 if __name__ == "__main__":
