@@ -324,10 +324,21 @@ def run_reference(args):
 
 def ncu_case(spec, scale):
     """Small profiling case: one app in one forced mode, host-driven loop (ncu cannot
-    profile kernels inside graphs with conditional nodes), run twice."""
+    profile kernels inside graphs with conditional nodes), run twice; or
+    batch_sssp:K — K sources at once in the persistent kernel."""
     import paper_2010_08781_gb300 as ipg
     app, mode = spec.split(":")
     g = build_graph(scale)
+    if app == "batch_sssp":
+        import inputs
+        k = int(mode)
+        src = np.concatenate([[0], inputs.uniform_vertices(g.n, k - 1, seed=1)]).astype(np.uint32)
+        with ipg.Graph.from_inputs(g) as G:
+            for _ in range(2):
+                _, st = G.run_batch_sssp(src)
+        print(json.dumps({"ncu_case": spec, "scale": scale, "edges": g.m, "supersteps": st["supersteps"],
+                          "ms": round(st["elapsed_ms"], 4), "messages": st["messages"]}))
+        return
     with ipg.Graph.from_inputs(g) as G:
         for _ in range(2):
             kw = dict(policy="forced", forced_mode=mode) if app != "pagerank" or mode != "auto" else {}

@@ -187,6 +187,42 @@ int ip_get_values(ip_graph_t* g, void* dst, size_t dst_bytes, int dst_is_device,
 #define IP_SELECTOR_BYTES (16 * 4 + (32 * 8 + 32 * 32 + 3 * 32) * 2 + (32 + 32 + 3) * 4)
 int ip_set_selector(ip_graph_t* g, const void* blob, size_t bytes);
 
+/* ---------------------------------------------------------- batched runs
+ * Many independent runs in one persistent launch (not in the paper, whose runs
+ * are one at a time): one cooperative kernel holds the whole superstep loop
+ * (Section 4.2), its phases separated by a grid-wide barrier whose every wait is
+ * bounded (IP_E_TIMEOUT when a wait runs out; the kernel then exits), launched
+ * through a CUDA graph. Each run keeps the synchronous semantics of ip_run. */
+#define IP_BATCH_MAX_SOURCES 256
+typedef struct {
+    uint32_t supersteps;            /* supersteps of the batch (its longest run), superstep 0 included */
+    int32_t halted;                 /* 1: every run halted; 0: the superstep cap stopped the batch */
+    uint64_t messages;              /* messages sent, all runs */
+    uint32_t* instance_supersteps;  /* caller array of k entries, or NULL: supersteps each run
+                                       takes on its own (as ip_run would report) */
+    float elapsed_ms;               /* device time of the persistent launch */
+    uint64_t barrier_timeout_ns;    /* input: bound of every barrier wait; 0 = 2 seconds */
+} ip_batch_stats_t;
+
+/* SSSP (Fig. 10, weighted) from k sources at once on one graph: distances are held
+ * per vertex for all sources, so one read of an in-edge serves every source.
+ *   sources   k host uint32 vertex IDs, 1 <= k <= IP_BATCH_MAX_SOURCES.
+ *   dist_out  k x n_vertices uint32, source-major (dist_out[i*n + v]), host or device
+ *             memory per out_is_device; INF = 0xFFFFFFFF for unreachable vertices.
+ * Returns IP_OK, IP_E_MAXSTEPS, IP_E_TIMEOUT, IP_E_RANGE (k or a source out of range). */
+int ip_run_batch_sssp(ip_graph_t* g, const uint32_t* sources, uint32_t k, uint32_t* dist_out, int out_is_device,
+                      uint32_t max_supersteps, ip_batch_stats_t* stats, void* stream);
+
+/* Hashmin (Fig. 9) on k independent graphs held as one block-diagonal graph g:
+ * instance i owns vertices [instance_offsets[i], instance_offsets[i+1]) and no edge
+ * crosses instances (not checked).
+ *   instance_offsets  k+1 host uint32, from 0 to n_vertices, non-decreasing.
+ *   labels_out        n_vertices uint32, label of each vertex as an ID local to its
+ *                     instance (host or device memory per out_is_device).
+ * The handle's value array is used as scratch: ip_get_values returns IP_E_STATE after. */
+int ip_run_batch_hashmin(ip_graph_t* g, const uint32_t* instance_offsets, uint32_t k, uint32_t* labels_out,
+                         int out_is_device, uint32_t max_supersteps, ip_batch_stats_t* stats, void* stream);
+
 /* ---------------------------------------------------------- selector training
  * Kernels that train the learned mode selector (not in the paper: the paper
  * chooses push or pull with a compile flag, Section 4.3.2). The network is the

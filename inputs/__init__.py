@@ -183,6 +183,23 @@ def rmat_graph(scale: int, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1, symme
     return g
 
 
+def rmat_sized(n: int, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=1, symmetrize=True) -> Graph:
+    """R-MAT graph on exactly n vertices: edge_factor * n draws at scale ceil(log2 n),
+    keeping the draws whose endpoints are both below n."""
+    scale = max(1, int(np.ceil(np.log2(max(n, 2)))))
+    src, dst = rmat_edges(scale, edge_factor * n, a, b, c, seed)
+    keep = (src < n) & (dst < n)
+    g = from_edges(n, src[keep], dst[keep], symmetrize, name=f"rmat_n{n}")
+    g.meta.update(kind="rmat_sized", n=n, edge_factor=edge_factor, seed=seed)
+    return g
+
+
+def hashmin_instances(k=1000, lo=1000, hi=100000, edge_factor=8, seed=1):
+    """k R-MAT instances with log-uniform sizes in [lo, hi], symmetrised, seeds seed..seed+k-1."""
+    sizes = loguniform_ints(k, lo, hi, seed=seed)
+    return [rmat_sized(int(n), edge_factor, seed=seed + i) for i, n in enumerate(sizes)]
+
+
 def er_graph(n: int, m: int, seed=1, symmetrize=False, weighted=False, wseed=None) -> Graph:
     src, dst = er_edges(n, m, seed)
     g = from_edges(n, src, dst, symmetrize, weighted, seed if wseed is None else wseed, name=f"er{n}")

@@ -60,6 +60,12 @@ class RunStatsC(ctypes.Structure):
                 ("elapsed_ms", ctypes.c_float)]
 
 
+class BatchStatsC(ctypes.Structure):
+    _fields_ = [("supersteps", ctypes.c_uint32), ("halted", ctypes.c_int32), ("messages", ctypes.c_uint64),
+                ("instance_supersteps", _U32P), ("elapsed_ms", ctypes.c_float),
+                ("barrier_timeout_ns", ctypes.c_uint64)]
+
+
 class GraphInfo(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_uint32), ("n_edges", ctypes.c_uint64), ("max_out_degree", ctypes.c_uint32),
                 ("max_in_degree", ctypes.c_uint32), ("csc_is_csr", ctypes.c_uint32), ("weighted", ctypes.c_uint32),
@@ -71,7 +77,8 @@ _lib = None
 # every symbol include/ipregel.h declares
 EXPORTS = ("ip_options_default", "ip_graph_create", "ip_graph_destroy", "ip_graph_info", "ip_run", "ip_get_values",
            "ip_set_selector", "ip_strerror", "ip_hashmin_noalloc", "ip_mlp_workspace_bytes", "ip_mlp_forward",
-           "ip_mlp_backward", "ip_mlp_adam", "ip_mlp_pack")
+           "ip_mlp_backward", "ip_mlp_adam", "ip_mlp_pack", "ip_run_batch_sssp", "ip_run_batch_hashmin")
+BATCH_MAX_SOURCES = 256
 MLP_PARAMS = 32 * 8 + 32 + 32 * 32 + 32 + 3 * 32 + 3
 NOALLOC_MAX_VERTICES = 1 << 20
 
@@ -114,6 +121,11 @@ def load(build_if_missing: bool = True):
     L.ip_mlp_pack.argtypes = [vp, vp, vp, vp]
     for name in ("ip_mlp_forward", "ip_mlp_backward", "ip_mlp_adam", "ip_mlp_pack"):
         getattr(L, name).restype = ctypes.c_int
+    bs = ctypes.POINTER(BatchStatsC)
+    L.ip_run_batch_sssp.argtypes = [vp, _U32P, ctypes.c_uint32, vp, ctypes.c_int, ctypes.c_uint32, bs, vp]
+    L.ip_run_batch_hashmin.argtypes = [vp, _U32P, ctypes.c_uint32, vp, ctypes.c_int, ctypes.c_uint32, bs, vp]
+    L.ip_run_batch_sssp.restype = ctypes.c_int
+    L.ip_run_batch_hashmin.restype = ctypes.c_int
     L.ip_strerror.argtypes = [ctypes.c_int]
     L.ip_strerror.restype = ctypes.c_char_p
     for name in ("ip_graph_create", "ip_graph_info", "ip_run", "ip_get_values", "ip_set_selector"):
@@ -292,6 +304,38 @@ class Graph:
         else:
             _check(L.ip_get_values(self._h, out.ctypes.data, out.nbytes, 0, st), "ip_get_values")
         return out
+
+    def _batch(self, fn, arr, k, out, out_rows, max_supersteps, stream, barrier_timeout_ns):
+        L = load()
+        arr = np.ascontiguousarray(arr, dtype=np.uint32)
+        per = np.zeros(k, np.uint32)
+        st = BatchStatsC()
+        st.instance_supersteps = per.ctypes.data_as(_U32P)
+        st.barrier_timeout_ns = int(barrier_timeout_ns)
+        if out is None:
+            out = np.empty((out_rows, self.n) if out_rows else self.n, np.uint32)
+        if _is_torch(out):
+            ptr, dev = out.data_ptr(), int(out.is_cuda)
+        else:
+            ptr, dev = out.ctypes.data, 0
+        code = getattr(L, fn)(self._h, arr.ctypes.data_as(_U32P), k, ptr, dev, int(max_supersteps),
+                              ctypes.byref(st), _stream_handle(stream))
+        if code not in (IP_OK, IP_E_MAXSTEPS):
+            raise IPError(code, fn)
+        return out, dict(code=code, supersteps=st.supersteps, halted=bool(st.halted), messages=st.messages,
+                         instance_supersteps=per, elapsed_ms=st.elapsed_ms)
+
+    def run_batch_sssp(self, sources, out=None, max_supersteps=100000, stream=None, barrier_timeout_ns=0):
+        """SSSP from every source in one persistent launch: (dist[k, n], stats)."""
+        k = len(sources)
+        return self._batch("ip_run_batch_sssp", sources, k, out, k, max_supersteps, stream, barrier_timeout_ns)
+
+    def run_batch_hashmin(self, instance_offsets, out=None, max_supersteps=100000, stream=None,
+                          barrier_timeout_ns=0):
+        """Hashmin of every block-diagonal instance in one persistent launch: (local labels[n], stats)."""
+        k = len(instance_offsets) - 1
+        return self._batch("ip_run_batch_hashmin", instance_offsets, k, out, 0, max_supersteps, stream,
+                           barrier_timeout_ns)
 
     def set_selector(self, blob: bytes):
         b = bytes(blob)

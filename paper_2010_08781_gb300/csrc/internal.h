@@ -171,6 +171,7 @@ struct ip_graph {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int grid[16] = {0};
     bool grids_ready = false;
+    void* batch = nullptr;  // state of the batched runs (batch.cu)
 };
 
 namespace ipg {
@@ -178,6 +179,8 @@ namespace ipg {
 int alloc_dev(ip_graph* g, void** p, size_t bytes);
 int ensure_bins(ip_graph* g, uint32_t t1, uint32_t t2, cudaStream_t st);
 int cuda_err(cudaError_t e);
+// batch.cu
+void free_batch_state(ip_graph* g);
 // superstep.cu
 int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* opt, ip_run_stats_t* stats);
 void free_graph_exec(ip_graph* g);
