@@ -26,7 +26,7 @@ namespace ipg {
 namespace {
 
 constexpr int BB = 256;            // threads per CTA of the persistent kernels
-constexpr uint32_t MS_CH = 512;    // in-edges per exchange task of the multi-source kernel
+constexpr uint32_t MS_CH = 128;    // in-edges per exchange task of the multi-source kernel
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 
 struct GridBar {
@@ -144,69 +144,85 @@ __device__ __forceinline__ void load_masks(const uint32_t* base, uint32_t u, boo
     }
 }
 
+// Per-warp scratch of the exchange phase.
+struct MsWarpSmem {
+    uint4 pairs[32 * 8];  // active (in-edge, group): {source vertex u, weight, mask word, group}
+    uint32_t cand[8 * 32];  // candidate minimum per (group, source lane)
+};
+
+// One exchange task: in-edges [b, e) of vertex v. Each batch of 32 in-edges is
+// turned into a list of active (in-edge, group) pairs; each pair costs one
+// 128-byte read of the sender's distances, eight pairs in flight at a time.
 template <int G, int GP>
-__device__ void ms_exchange_task(const MsParams& P, const uint32_t* prev, uint2 task) {
+__device__ void ms_exchange_task(const MsParams& P, const uint32_t* prev, uint2 task, MsWarpSmem& S) {
     const uint32_t lane = lane_of();
     const uint32_t v = task.x & 0x7FFFFFFFu;
     const bool multi = task.x >> 31;
     const uint32_t b = task.y, e = min(b + MS_CH, P.csc_off[v + 1]);
-    uint32_t cand[G], rb[G];
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-        cand[g] = INF;
-        rb[g] = 0;
-    }
+    for (int g = 0; g < G; ++g) S.cand[g * 32 + lane] = INF;
+    uint32_t rb[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) rb[g] = 0;
     for (uint32_t base = b; base < e; base += 32) {
         const uint32_t ei = base + lane;
         const bool valid = ei < e;
         const uint32_t u = valid ? P.csc_row[ei] : 0u;
         uint32_t mw[GP];
         load_masks<GP>(prev, u, valid, mw);
-        uint32_t anyw = 0;
+        uint32_t cnt = 0;
 #pragma unroll
-        for (int g = 0; g < G; ++g) anyw |= mw[g];
-        if (!__any_sync(FULL, anyw != 0)) continue;  // no in-neighbour of this batch broadcast
+        for (int g = 0; g < G; ++g) cnt += mw[g] != 0;
+        uint32_t inc = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= (uint32_t)o) inc += y;
+        }
+        const uint32_t total = __shfl_sync(FULL, inc, 31);
+        if (!total) continue;  // no in-neighbour of this batch broadcast
         const uint32_t w = valid ? (P.csc_w ? P.csc_w[ei] : 1u) : 0u;
+        uint32_t pos = inc - cnt;
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            uint32_t act = __ballot_sync(FULL, mw[g] != 0);
-            if (!act) continue;
             rb[g] |= __reduce_or_sync(FULL, mw[g]);
-            while (act) {  // up to four senders of this batch per round, loads in flight together
-                uint32_t j[4], m[4], x[4];
+            if (mw[g]) S.pairs[pos++] = make_uint4(u, w, mw[g], (uint32_t)g);
+        }
+        __syncwarp();
+        for (uint32_t p0 = 0; p0 < total; p0 += 8) {
+            uint32_t x[8];
+            uint4 pr[8];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    j[q] = act ? (uint32_t)(__ffs(act) - 1) : 32u;
-                    if (act) act &= act - 1;
+            for (int q = 0; q < 8; ++q) {
+                const bool in = p0 + q < total;
+                pr[q] = in ? S.pairs[p0 + q] : make_uint4(0, 0, 0, 0);
+                const bool take = in && ((pr[q].z >> lane) & 1u);
+                x[q] = take ? ldcg(P.dist + slot(pr[q].x, G, pr[q].w) + lane) : INF;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (x[q] != INF) {
+                    uint32_t* c = &S.cand[pr[q].w * 32 + lane];
+                    *c = min(*c, sat_add32(x[q], pr[q].y));
                 }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t jj = j[q] & 31u;
-                    m[q] = __shfl_sync(FULL, mw[g], jj);
-                    const uint32_t uj = __shfl_sync(FULL, u, jj);
-                    const bool take = j[q] < 32u && ((m[q] >> lane) & 1u);
-                    x[q] = take ? ldcg(P.dist + slot(uj, G, g) + lane) : INF;
-                    m[q] = __shfl_sync(FULL, w, jj);
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (x[q] != INF) cand[g] = min(cand[g], sat_add32(x[q], m[q]));
             }
         }
+        __syncwarp();
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         if (!rb[g]) continue;
         const size_t idx = slot(v, G, g) + lane;
         const uint32_t ri = v * GP + g;
+        const uint32_t cg = S.cand[g * 32 + lane];
         if (multi) {
-            if ((rb[g] >> lane) & 1u) atomicMin(P.mbox + idx, cand[g]);
+            if ((rb[g] >> lane) & 1u) atomicMin(P.mbox + idx, cg);
             if (lane == 0) atomicOr(P.rmask + ri, rb[g]);
         } else {
-            if ((rb[g] >> lane) & 1u) P.mbox[idx] = cand[g];
+            if ((rb[g] >> lane) & 1u) P.mbox[idx] = cg;
             if (lane == 0) P.rmask[ri] = rb[g];
         }
     }
+    __syncwarp();
 }
 
 template <int G, int GP>
@@ -287,6 +303,7 @@ __global__ void __launch_bounds__(BB) k_msssp(MsParams P) {
             P.msgs[2] = t;
             P.state[0] = 1;
             P.state[1] = 0;
+            P.state[2] = P.state[3] = 0;  // task counters of the exchange phase, by parity
         }
     }
     if (!grid_sync(P.bar, P.limit_ns)) return;
@@ -302,7 +319,19 @@ __global__ void __launch_bounds__(BB) k_msssp(MsParams P) {
         const uint32_t* prev = (s & 1) ? P.mask0 : P.mask1;
         uint32_t* next = (s & 1) ? P.mask1 : P.mask0;
         if (blockIdx.x == 0 && threadIdx.x == 0) P.msgs[s & 1] = 0;
-        for (uint32_t t = gw; t < P.n_tasks; t += nw) ms_exchange_task<G, GP>(P, prev, P.tasks[t]);
+        {  // tasks are claimed four at a time from a counter; the largest come first
+            __shared__ MsWarpSmem smem[BB / 32];
+            MsWarpSmem& S = smem[threadIdx.x >> 5];
+            unsigned int* ctr = P.state + 2 + (s & 1);
+            if (blockIdx.x == 0 && threadIdx.x == 0) P.state[2 + ((s + 1) & 1)] = 0;  // next superstep's counter
+            while (true) {
+                uint32_t t0 = 0;
+                if (lane == 0) t0 = atomicAdd(ctr, 4u);
+                t0 = __shfl_sync(FULL, t0, 0);
+                if (t0 >= P.n_tasks) break;
+                for (uint32_t t = t0; t < min(t0 + 4, P.n_tasks); ++t) ms_exchange_task<G, GP>(P, prev, P.tasks[t], S);
+            }
+        }
         if (!grid_sync(P.bar, P.limit_ns)) return;
         unsigned long long mine = 0;
         for (uint32_t v = gw; v < P.V; v += nw) mine += ms_apply_vertex<G, GP>(P, next, v, s);
@@ -702,6 +731,12 @@ int ip_run_batch_sssp(ip_graph_t* g, const uint32_t* sources, uint32_t k, uint32
             const uint32_t flag = d > MS_CH ? 0x80000000u : 0u;
             for (uint32_t c = 0; c < d; c += MS_CH) tasks.push_back(make_uint2(v | flag, off[v] + c));
         }
+        // largest tasks first (they are claimed in list order)
+        auto len = [&](const uint2& t) {
+            const uint32_t v = t.x & 0x7FFFFFFFu;
+            return std::min(MS_CH, off[v + 1] - t.y);
+        };
+        std::stable_sort(tasks.begin(), tasks.end(), [&](const uint2& a, const uint2& b) { return len(a) > len(b); });
         if ((r = alloc_dev(g, (void**)&b->tasks, std::max<size_t>(tasks.size(), 1) * sizeof(uint2)))) return r;
         if (!tasks.empty())
             CKB(cudaMemcpyAsync(b->tasks, tasks.data(), tasks.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
