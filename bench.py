@@ -347,6 +347,84 @@ def ncu_case(spec, scale):
                       "ms": round(st.elapsed_ms, 4)}))
 
 
+def pr_measure(G, V, E, reps=3, T=30):
+    """PageRank pull, T iterations: device time of the run and the k_pr_pull roofline
+    (8E + 16V + 4(V+1) algorithmic bytes per launch, CUDA events per launch)."""
+    peak, kind = measured_peaks()
+    ts = [G.run("pagerank", policy="forced", forced_mode="pull", pr_iterations=T).elapsed_ms for _ in range(reps)]
+    st = G.run("pagerank", policy="forced", forced_mode="pull", pr_iterations=T, profile_kernels=1)
+    kms = [float(x) for x in st.kernel_ms[1:st.supersteps, 1]]
+    by = 4 * (V + 1) + 8 * E + 16 * V
+    avg = sum(kms) / len(kms)
+    ach = by / (avg * 1e-3) / 1e9
+    return {"gteps": round(T * E / (min(ts) * 1e-3) / 1e9, 2), "ms": round(min(ts), 4),
+            "roofline": {"bound": "hbm", "kernel": "k_pr_pull", "achieved": round(ach, 1), "peak": peak,
+                         "peak_kind": kind, "unit": "GB/s", "frac": round(ach / peak, 4),
+                         "avg_launch_us": round(1e3 * avg, 2), "bytes_per_launch": by}}
+
+
+def run_config(args):
+    """Secondary measured configurations (one JSON line each)."""
+    import paper_2010_08781_gb300 as ipg
+    import inputs
+    import torch
+    torch.cuda.set_device(0)
+    out = {"config": args.config}
+    if args.config == "c1":  # PageRank, directed R-MAT scale 16, T = 30
+        g = inputs.rmat_graph(16, seed=1)
+        with ipg.Graph.from_inputs(g) as G:
+            out["pagerank"] = pr_measure(G, g.n, g.m)
+        out["workload"] = "PageRank T=30 on directed R-MAT scale 16 (edge factor 16, seed 1)"
+        out["edges"] = g.m
+    elif args.config == "c4":  # batched
+        g = inputs.rmat_graph(20, symmetrize=True, weighted=True, seed=1)
+        src = np.concatenate([[0], inputs.uniform_vertices(g.n, 255, seed=1)]).astype(np.uint32)
+        with ipg.Graph.from_inputs(g) as G:
+            G.run_batch_sssp(src)
+            rs = [G.run_batch_sssp(src)[1] for _ in range(3)]
+            seq = [G.run("sssp", source=int(s)).elapsed_ms for s in src[:32]]
+        best = min(r["elapsed_ms"] for r in rs)
+        out["batch_sssp"] = {"sources": 256, "ms": round(best, 3), "supersteps": rs[0]["supersteps"],
+                             "messages": rs[0]["messages"],
+                             "gteps": round(rs[0]["messages"] / (best * 1e-3) / 1e9, 2),
+                             "sequential_ms_estimate": round(sum(seq) * 256 / 32, 2)}
+        del g
+        gs = inputs.hashmin_instances(1000, seed=1)
+        u, offs = inputs.block_diagonal(gs)
+        with ipg.Graph.from_inputs(u) as G:
+            G.run_batch_hashmin(offs.astype(np.uint32))
+            rs = [G.run_batch_hashmin(offs.astype(np.uint32))[1] for _ in range(3)]
+            pers = min(G.run_batch_hashmin(offs.astype(np.uint32), engine="persistent")[1]["elapsed_ms"]
+                       for _ in range(3))
+            single = min(G.run("hashmin").elapsed_ms for _ in range(3))
+        best = min(r["elapsed_ms"] for r in rs)
+        out["batch_hashmin"] = {"instances": 1000, "vertices": u.n, "edges": u.m, "ms": round(best, 3),
+                                "supersteps": rs[0]["supersteps"], "messages": rs[0]["messages"],
+                                "gteps": round(rs[0]["messages"] / (best * 1e-3) / 1e9, 2),
+                                "persistent_engine_ms": round(pers, 3), "ip_run_union_ms": round(single, 3)}
+        out["workload"] = ("256 SSSP sources on symmetrised weighted R-MAT scale 20; 1,000 Hashmin instances, "
+                           "R-MAT 1k-100k vertices (log-uniform), edge factor 8, symmetrised")
+    elif args.config == "c5":  # billion-edge
+        g = inputs.rmat_graph(26, seed=1)
+        V, E = g.n, g.m
+        with ipg.Graph(V, g.row_ptr, g.col) as G:  # in-edges transposed on the device
+            del g
+            out["pagerank"] = pr_measure(G, V, E, reps=2)
+            out["pagerank"]["vertices"], out["pagerank"]["edges"] = V, E
+        src, dst = inputs.rmat_edges(26, 16 << 26, seed=1)
+        gs = inputs.from_edges(1 << 26, src, dst, symmetrize=True)
+        del src, dst
+        with ipg.Graph.from_inputs(gs) as G:
+            ts = [G.run("hashmin") for _ in range(2)]
+        best = min(ts, key=lambda r: r.elapsed_ms)
+        m = int(best.messages.sum())
+        out["hashmin_symmetrised"] = {"vertices": gs.n, "edges": gs.m, "ms": round(best.elapsed_ms, 3),
+                                      "supersteps": best.supersteps, "gteps": round(m / (best.elapsed_ms * 1e-3) / 1e9, 2),
+                                      "modes": best.mode[1:].tolist()}
+        out["workload"] = "R-MAT scale 26, edge factor 16, seed 1: PageRank T=30 pull (directed), Hashmin (symmetrised)"
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,7 +435,12 @@ def main():
     ap.add_argument("--policy", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", default=None, help="APP:MODE, e.g. sssp:pull — small profiling case only")
+    ap.add_argument("--config", default=None, choices=["c1", "c4", "c5"],
+                    help="secondary configurations: c1 PageRank scale 16, c4 batched, c5 scale 26")
     args = ap.parse_args()
+    if args.config:
+        run_config(args)
+        return
     if args.ncu_case:
         ncu_case(args.ncu_case, args.scale)
         return

@@ -202,6 +202,9 @@ typedef struct {
                                        takes on its own (as ip_run would report) */
     float elapsed_ms;               /* device time of the persistent launch */
     uint64_t barrier_timeout_ns;    /* input: bound of every barrier wait; 0 = 2 seconds */
+    int32_t engine;                 /* input, Hashmin batches: 0 = the device-driven superstep graph
+                                       of ip_run (all exchange modes, default), 1 = the persistent
+                                       cooperative pull kernel */
 } ip_batch_stats_t;
 
 /* SSSP (Fig. 10, weighted) from k sources at once on one graph: distances are held
@@ -213,7 +216,9 @@ typedef struct {
 int ip_run_batch_sssp(ip_graph_t* g, const uint32_t* sources, uint32_t k, uint32_t* dist_out, int out_is_device,
                       uint32_t max_supersteps, ip_batch_stats_t* stats, void* stream);
 
-/* Hashmin (Fig. 9) on k independent graphs held as one block-diagonal graph g:
+/* Hashmin (Fig. 9) on k independent graphs held as one block-diagonal graph g,
+ * in one launch (engine 0: one CUDA-graph launch whose superstep loop runs on the
+ * device; engine 1: one persistent cooperative kernel):
  * instance i owns vertices [instance_offsets[i], instance_offsets[i+1]) and no edge
  * crosses instances (not checked).
  *   instance_offsets  k+1 host uint32, from 0 to n_vertices, non-decreasing.

@@ -63,7 +63,7 @@ class RunStatsC(ctypes.Structure):
 class BatchStatsC(ctypes.Structure):
     _fields_ = [("supersteps", ctypes.c_uint32), ("halted", ctypes.c_int32), ("messages", ctypes.c_uint64),
                 ("instance_supersteps", _U32P), ("elapsed_ms", ctypes.c_float),
-                ("barrier_timeout_ns", ctypes.c_uint64)]
+                ("barrier_timeout_ns", ctypes.c_uint64), ("engine", ctypes.c_int32)]
 
 
 class GraphInfo(ctypes.Structure):
@@ -165,9 +165,28 @@ def _ptr(a):
     return arr.ctypes.data, False, arr
 
 
-def default_options(**kw) -> Options:
+_TUNED = None
+
+
+def tuned_defaults() -> dict:
+    """Per-app cutoffs written by the autotuner (tuned_defaults.json), or {}."""
+    global _TUNED
+    if _TUNED is None:
+        import json
+        p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_defaults.json")
+        _TUNED = json.load(open(p)) if os.path.exists(p) else {}
+    return _TUNED
+
+
+def default_options(app=None, **kw) -> Options:
+    """Options with the library defaults, the autotuned cutoffs for `app`, then kw."""
     o = Options()
     load().ip_options_default(ctypes.byref(o))
+    t = tuned_defaults()
+    if app is not None and app in t.get("bins", {}):
+        o.t1, o.t2 = t["bins"][app]["t1"], t["bins"][app]["t2"]
+    if "modes" in t:
+        o.thr_sparse, o.thr_pull = t["modes"]["thr_sparse"], t["modes"]["thr_pull"]
     seq = kw.pop("mode_sequence", None)
     for k, v in kw.items():
         if k == "policy" and isinstance(v, str):
@@ -265,8 +284,9 @@ class Graph:
         return {k: getattr(i, k) for k, _ in GraphInfo._fields_}
 
     def run(self, app, max_supersteps=100000, stats_capacity=1024, raise_on_maxsteps=False, **opts) -> RunStats:
-        app = APPS[app] if isinstance(app, str) else int(app)
-        o = default_options(**opts)
+        name = app if isinstance(app, str) else {v: k for k, v in APPS.items()}[int(app)]
+        app = APPS[name]
+        o = default_options(name, **opts)
         cap = stats_capacity
         arr = dict(mode=np.zeros(cap, np.uint8), active=np.zeros(cap, np.uint32),
                    broadcasters=np.zeros(cap, np.uint32), messages=np.zeros(cap, np.uint64),
@@ -305,13 +325,14 @@ class Graph:
             _check(L.ip_get_values(self._h, out.ctypes.data, out.nbytes, 0, st), "ip_get_values")
         return out
 
-    def _batch(self, fn, arr, k, out, out_rows, max_supersteps, stream, barrier_timeout_ns):
+    def _batch(self, fn, arr, k, out, out_rows, max_supersteps, stream, barrier_timeout_ns, engine=0):
         L = load()
         arr = np.ascontiguousarray(arr, dtype=np.uint32)
         per = np.zeros(k, np.uint32)
         st = BatchStatsC()
         st.instance_supersteps = per.ctypes.data_as(_U32P)
         st.barrier_timeout_ns = int(barrier_timeout_ns)
+        st.engine = int(engine)
         if out is None:
             out = np.empty((out_rows, self.n) if out_rows else self.n, np.uint32)
         if _is_torch(out):
@@ -331,11 +352,12 @@ class Graph:
         return self._batch("ip_run_batch_sssp", sources, k, out, k, max_supersteps, stream, barrier_timeout_ns)
 
     def run_batch_hashmin(self, instance_offsets, out=None, max_supersteps=100000, stream=None,
-                          barrier_timeout_ns=0):
-        """Hashmin of every block-diagonal instance in one persistent launch: (local labels[n], stats)."""
+                          barrier_timeout_ns=0, engine="graph"):
+        """Hashmin of every block-diagonal instance in one launch: (local labels[n], stats).
+        engine: "graph" (device-driven superstep graph) or "persistent" (cooperative kernel)."""
         k = len(instance_offsets) - 1
         return self._batch("ip_run_batch_hashmin", instance_offsets, k, out, 0, max_supersteps, stream,
-                           barrier_timeout_ns)
+                           barrier_timeout_ns, 0 if engine == "graph" else 1)
 
     def set_selector(self, blob: bytes):
         b = bytes(blob)

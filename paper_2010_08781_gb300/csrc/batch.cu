@@ -528,6 +528,39 @@ __global__ void k_bh_local(const BhParams P, uint32_t* out) {
         out[v] = P.label[v] - __ldg(P.inst_off + instance_of(P, v));
 }
 
+// Engine 0 helpers: per-instance maximum of the per-vertex last-send record
+// (1 + superstep, 0 = never), and labels local to each instance.
+__global__ void k_inst_max(const uint32_t* track, const uint32_t* off, uint32_t k, uint32_t* inst_last) {
+    __shared__ uint32_t sh[BB / 32];
+    for (uint32_t i = blockIdx.x; i < k; i += gridDim.x) {
+        uint32_t m = 0;
+        for (uint32_t v = off[i] + threadIdx.x; v < off[i + 1]; v += blockDim.x) m = max(m, track[v]);
+        m = __reduce_max_sync(FULL, m);
+        if (lane_of() == 0) sh[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = max(t, sh[w]);
+            inst_last[i] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_local_labels(const uint32_t* label, uint32_t V, const uint32_t* off, uint32_t k, uint32_t* out) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = k;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (off[mid] <= v)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        out[v] = label[v] - off[lo];
+    }
+}
+
 // =================================================================== host state
 struct BatchState {
     // multi-source SSSP
@@ -546,6 +579,7 @@ struct BatchState {
     GridBar* bar = nullptr;
     uint32_t* out_tmp = nullptr;  // host-bound outputs staged on the device
     size_t out_cap = 0;
+    uint32_t* track = nullptr;    // per-vertex last-send record (engine 0 Hashmin batches)
     cudaGraphExec_t exec = nullptr;
     unsigned char key[256] = {0};
     size_t key_len = 0;
@@ -682,7 +716,7 @@ void free_batch_state(ip_graph* g) {
     if (!g->batch) return;
     BatchState* b = (BatchState*)g->batch;
     drop_exec(b);
-    void* bufs[] = {b->dist, b->mbox, b->masks, b->tasks, b->small, b->msgs, b->state, b->bar, b->out_tmp};
+    void* bufs[] = {b->dist, b->mbox, b->masks, b->tasks, b->small, b->msgs, b->state, b->bar, b->out_tmp, b->track};
     for (void* p : bufs)
         if (p) cudaFree(p);
     delete b;
@@ -813,6 +847,52 @@ int ip_run_batch_hashmin(ip_graph_t* g, const uint32_t* instance_offsets, uint32
     int r;
     if ((r = ensure_bins(g, g->bins_t1 ? g->bins_t1 : DEFAULT_T1, g->bins_t2 ? g->bins_t2 : DEFAULT_T2, st))) return r;
     if ((r = ensure_small(g, b, 2 * (size_t)k + 1))) return r;
+    if (!stats || stats->engine == 0) {
+        // the union runs through ip_run's device-driven superstep graph, recording last sends
+        if (!b->track && (r = alloc_dev(g, (void**)&b->track, (size_t)g->V * 4))) return r;
+        CKB(cudaMemcpyAsync(b->small, instance_offsets, ((size_t)k + 1) * 4, cudaMemcpyHostToDevice, st));
+        ip_options_t o;
+        ip_options_default(&o);
+        o.stream = stream;
+        const uint32_t cap = std::min<uint32_t>(max_supersteps, 1u << 16);
+        std::vector<uint64_t> msgs(cap);
+        ip_run_stats_t rs;
+        memset(&rs, 0, sizeof(rs));
+        rs.capacity = cap;
+        rs.messages = msgs.data();
+        g->track_send = b->track;
+        r = run_app(g, APP_HM, max_supersteps, &o, &rs);
+        g->track_send = nullptr;
+        if (r != IP_OK && r != IP_E_MAXSTEPS) return r;
+        uint32_t* inst_last = b->small + k + 1;
+        k_inst_max<<<std::min<uint32_t>(k, (uint32_t)g->num_sms * 8), BB, 0, st>>>(b->track, b->small, k, inst_last);
+        uint32_t* out = labels_out;
+        if (!out_is_device) {
+            int r2 = ensure_out(g, b, g->V);
+            if (r2) return r2;
+            out = b->out_tmp;
+        }
+        k_local_labels<<<g->num_sms * 8, 256, 0, st>>>(g->value, g->V, b->small, k, out);
+        CKB(cudaGetLastError());
+        if (!out_is_device) CKB(cudaMemcpyAsync(labels_out, out, (size_t)g->V * 4, cudaMemcpyDeviceToHost, st));
+        if (stats) {
+            stats->supersteps = rs.supersteps;
+            stats->halted = rs.halted;
+            stats->elapsed_ms = rs.elapsed_ms;
+            uint64_t tot = 0;
+            for (uint32_t i = 0; i < std::min(rs.supersteps, cap); ++i) tot += msgs[i];
+            stats->messages = tot;
+            if (stats->instance_supersteps) {
+                std::vector<uint32_t> last(k);
+                CKB(cudaMemcpyAsync(last.data(), inst_last, (size_t)k * 4, cudaMemcpyDeviceToHost, st));
+                CKB(cudaStreamSynchronize(st));
+                for (uint32_t i = 0; i < k; ++i) stats->instance_supersteps[i] = last[i] == 0 ? 1u : last[i] + 1u;
+            }
+        }
+        CKB(cudaStreamSynchronize(st));
+        g->last_app = -1;
+        return r;
+    }
     CKB(cudaMemcpyAsync(b->small, instance_offsets, ((size_t)k + 1) * 4, cudaMemcpyHostToDevice, st));
     CKB(cudaMemsetAsync(b->small + k + 1, 0xFF, (size_t)k * 4, st));
     CKB(cudaMemsetAsync(b->msgs, 0, 4 * sizeof(unsigned long long), st));

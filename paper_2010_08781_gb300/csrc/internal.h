@@ -101,6 +101,7 @@ struct Params {
     uint32_t* q[2][2];  // broadcaster queues [parity][small, medium]
     uint2* hq[2];       // heavy broadcaster chunks [parity]: {vertex, chunk index}
     DevCtl* ctl;
+    uint32_t* last_send;  // optional [V]: 1 + last superstep in which the vertex sent a message (0 = never)
     LogRec* log;
     uint32_t log_cap;
     const SelectorDev* sel;
@@ -171,7 +172,8 @@ struct ip_graph {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int grid[16] = {0};
     bool grids_ready = false;
-    void* batch = nullptr;  // state of the batched runs (batch.cu)
+    void* batch = nullptr;        // state of the batched runs (batch.cu)
+    uint32_t* track_send = nullptr;  // when set, runs record per-vertex last sends here (batched Hashmin)
 };
 
 namespace ipg {

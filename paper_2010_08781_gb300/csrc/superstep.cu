@@ -166,6 +166,7 @@ __global__ void k_init_min(Params P) {
         P.value[v] = x;
         P.outbox[v] = x;  // every initial value below INF is broadcast
         P.mbox[v] = INF;
+        if (P.last_send) P.last_send[v] = (x != INF && P.csr_off[v + 1] > P.csr_off[v]) ? 1u : 0u;
     }
     for (uint32_t w = tid; w < P.W; w += nth) {
         P.recv[w] = 0;
@@ -499,6 +500,7 @@ __device__ __forceinline__ bool apply_vertex(const Params& P, uint32_t v, uint32
     if (m < val) {
         P.value[v] = m;
         deg = P.csr_off[v + 1] - P.csr_off[v];
+        if (P.last_send && deg) P.last_send[v] = P.ctl->superstep + 1;
         return true;  // broadcast the new value
     }
     return false;
@@ -545,6 +547,7 @@ __global__ void __launch_bounds__(BLOCK) k_apply_bitmap(Params P) {
             const uint32_t v = w * 32 + lane;
             const bool b = deg[k] != 0;
             deg[k] = b ? P.csr_off[v + 1] - P.csr_off[v] : 0u;
+            if (P.last_send && deg[k]) P.last_send[v] = P.ctl->superstep + 1;
             const uint32_t bb = __ballot_sync(FULL, b);
             if (lane == 0 && w < words) {
                 bc[w] = bb;
@@ -1204,6 +1207,7 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
         P.hq[p] = g->hq[p];
     }
     P.ctl = g->ctl;
+    P.last_send = g->track_send;
     P.log = g->log;
     P.log_cap = g->log_cap;
     P.sel = g->sel;

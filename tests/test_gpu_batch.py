@@ -54,19 +54,23 @@ def test_batch_sssp_duplicate_sources_and_cap():
         assert st["code"] == ipg.IP_E_MAXSTEPS and st["supersteps"] == 5
 
 
-def test_batch_hashmin_matches_oracle():
+@pytest.mark.parametrize("engine", ["graph", "persistent"])
+def test_batch_hashmin_matches_oracle(engine):
     rng = np.random.default_rng(4)
     gs = [inputs.rmat_sized(int(n), 8, seed=100 + i) for i, n in enumerate(rng.integers(1, 3000, 25))]
     gs.append(inputs.empty_graph(7))
     u, offs = inputs.block_diagonal(gs)
     with ipg.Graph.from_inputs(u) as G:
-        labels, st = G.run_batch_hashmin(offs.astype(np.uint32))
+        labels, st = G.run_batch_hashmin(offs.astype(np.uint32), engine=engine)
     assert st["halted"]
+    m = 0
     for i, h in enumerate(gs):
         want, ost = oracle.hashmin(h.n, h.row_ptr, h.col)
         assert np.array_equal(labels[offs[i]:offs[i + 1]], want), i
         assert st["instance_supersteps"][i] == ost["supersteps"], i
+        m += int(ost["messages"].sum())
     assert st["supersteps"] == max(st["instance_supersteps"])
+    assert st["messages"] == m
 
 
 def test_batch_errors_and_bounded_barrier_timeout():
@@ -103,10 +107,11 @@ def test_batch_full_size_sampled():
     gs = inputs.hashmin_instances(1000, seed=1)
     u, offs = inputs.block_diagonal(gs)
     with ipg.Graph.from_inputs(u) as G:
-        labels, st = G.run_batch_hashmin(offs.astype(np.uint32))
-    assert st["halted"]
-    for i in (0, 1, 499, 998, 999):
-        h = gs[i]
-        want, ost = oracle.hashmin(h.n, h.row_ptr, h.col)
-        assert np.array_equal(labels[offs[i]:offs[i + 1]], want), i
-        assert st["instance_supersteps"][i] == ost["supersteps"], i
+        for engine in ("graph", "persistent"):
+            labels, st = G.run_batch_hashmin(offs.astype(np.uint32), engine=engine)
+            assert st["halted"]
+            for i in (0, 1, 499, 998, 999):
+                h = gs[i]
+                want, ost = oracle.hashmin(h.n, h.row_ptr, h.col)
+                assert np.array_equal(labels[offs[i]:offs[i + 1]], want), (engine, i)
+                assert st["instance_supersteps"][i] == ost["supersteps"], (engine, i)
