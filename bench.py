@@ -145,6 +145,21 @@ KERNEL_NAMES = {("pull", "hashmin"): "k_pull<Hashmin>", ("pull", "sssp"): "k_pul
 MODE_NAMES = {0: "push_sparse", 1: "push_dense", 2: "pull"}
 
 
+# ----------------------------------------------------------------- replicas
+def reduce_over_ranks(total_ms, msgs, world, device=None):
+    """Whole-job figures of independent replicas: the slowest rank's time and the
+    messages of all ranks (no data-path collective; two scalars per run)."""
+    if world <= 1:
+        return float(total_ms), float(msgs)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms), float(msgs)], dtype=torch.float64, device=device)
+    tmax, tsum = t.clone(), t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0].item()), float(tsum[1].item())
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world, local_rank):
     import torch
@@ -192,17 +207,7 @@ def run_gpu(args, rank, world, local_rank):
             per_app["sssp"].append(b)
         torch.cuda.synchronize()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        m = torch.tensor([msgs], dtype=torch.float64, device=dev)
-        dist.all_reduce(m, op=dist.ReduceOp.SUM)
-        msgs_all = float(m.item())
-    else:
-        msgs_all = float(msgs)
+    total_ms, msgs_all = reduce_over_ranks(sum(step_ms), msgs, world, dev)
     value = msgs_all / (total_ms * 1e-3) / 1e9
 
     # ---------------------------------------------------------- roofline of the dominant kernel

@@ -845,7 +845,7 @@ int ip_run_batch_hashmin(ip_graph_t* g, const uint32_t* instance_offsets, uint32
     cudaStream_t st = (cudaStream_t)stream;
     BatchState* b = state_of(g);
     int r;
-    if ((r = ensure_bins(g, g->bins_t1 ? g->bins_t1 : DEFAULT_T1, g->bins_t2 ? g->bins_t2 : DEFAULT_T2, st))) return r;
+    if ((r = ensure_bins(g, g->cur ? g->cur->t1 : DEFAULT_T1, g->cur ? g->cur->t2 : DEFAULT_T2, st))) return r;
     if ((r = ensure_small(g, b, 2 * (size_t)k + 1))) return r;
     if (!stats || stats->engine == 0) {
         // the union runs through ip_run's device-driven superstep graph, recording last sends
@@ -904,8 +904,8 @@ int ip_run_batch_hashmin(ip_graph_t* g, const uint32_t* instance_offsets, uint32
     P.csr_off = g->csr_off;
     P.csc_off = g->csc_off;
     P.csc_row = g->csc_row;
-    P.bin = g->bins[1];
-    P.t1 = g->bins_t1;
+    P.bin = g->cur->b[1];
+    P.t1 = g->cur->t1;
     P.label = g->value;
     P.outbox = g->outbox;
     P.mbox = g->mbox;

@@ -169,28 +169,26 @@ static int grid_for(const ip_graph* g, uint64_t work) {
     return (int)(b ? b : 1);
 }
 
-static void free_bins(ip_graph* g, int k) {
-    for (int i = 0; i < 5; ++i) {
-        if (g->bin_mem[k][i]) {
-            cudaFree(g->bin_mem[k][i]);
-            g->device_bytes -= g->bin_bytes[k][i];
-        }
-        g->bin_mem[k][i] = nullptr;
-        g->bin_bytes[k][i] = 0;
-    }
-    g->bins[k] = Bins{};
+static void free_binset(ip_graph* g, BinSet* S) {
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < 5; ++i)
+            if (S->mem[k][i]) {
+                cudaFree(S->mem[k][i]);
+                g->device_bytes -= S->bytes[k][i];
+            }
+    delete S;
 }
 
-static int bin_alloc(ip_graph* g, int k, int i, size_t bytes) {
+static int bin_alloc(ip_graph* g, BinSet* S, int k, int i, size_t bytes) {
     bytes = bytes ? bytes : 16;
-    int r = alloc_dev(g, &g->bin_mem[k][i], bytes);
-    if (!r) g->bin_bytes[k][i] = bytes;
+    int r = alloc_dev(g, &S->mem[k][i], bytes);
+    if (!r) S->bytes[k][i] = bytes;
     return r;
 }
 
 // Static degree bins of one direction, built on the host from the offsets.
-static int build_bins(ip_graph* g, int k, const uint32_t* dev_off, uint32_t t1, uint32_t t2, cudaStream_t st) {
-    const uint32_t n = g->V;
+static int build_bins(ip_graph* g, BinSet* S, int k, const uint32_t* dev_off, cudaStream_t st) {
+    const uint32_t n = g->V, t1 = S->t1, t2 = S->t2;
     std::vector<uint32_t> off((size_t)n + 1);
     CK(cudaMemcpyAsync(off.data(), dev_off, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -211,14 +209,12 @@ static int build_bins(ip_graph* g, int k, const uint32_t* dev_off, uint32_t t1, 
             }
         }
     }
-    free_bins(g, k);
-    Bins& B = g->bins[k];
-    void** mem = g->bin_mem[k];
+    Bins& B = S->b[k];
+    void** mem = S->mem[k];
     int r;
     const size_t sz[5] = {med.size() * 4, chunks.size() * 16, hv.size() * 8, hv.size() * 4, chunks.size() * 8};
-    for (int i = 0; i < 5; ++i) {
-        if ((r = bin_alloc(g, k, i, sz[i]))) return r;
-    }
+    for (int i = 0; i < 5; ++i)
+        if ((r = bin_alloc(g, S, k, i, sz[i]))) return r;
     if (!med.empty()) CK(cudaMemcpyAsync(mem[0], med.data(), sz[0], cudaMemcpyHostToDevice, st));
     if (!chunks.empty()) CK(cudaMemcpyAsync(mem[1], chunks.data(), sz[1], cudaMemcpyHostToDevice, st));
     if (!hv.empty()) CK(cudaMemcpyAsync(mem[2], hv.data(), sz[2], cudaMemcpyHostToDevice, st));
@@ -235,36 +231,60 @@ static int build_bins(ip_graph* g, int k, const uint32_t* dev_off, uint32_t t1, 
     return IP_OK;
 }
 
+// Selects (building if needed) the degree bins for (t1, t2) as g->cur.
 int ensure_bins(ip_graph* g, uint32_t t1, uint32_t t2, cudaStream_t st) {
-    if (g->bins_t1 == t1 && g->bins_t2 == t2) return IP_OK;
-    g->bins_t1 = g->bins_t2 = 0;
-    int r;
-    if ((r = build_bins(g, 0, g->csr_off, t1, t2, st))) return r;
-    if (g->csc_alias) {
-        free_bins(g, 1);
-        // share the CSR bins except the PageRank finish state, which must be private
-        g->bins[1] = g->bins[0];
-        if ((r = bin_alloc(g, 1, 3, g->bins[0].n_hvert * 4 + 16))) return r;
-        if ((r = bin_alloc(g, 1, 4, g->bins[0].n_hchunk * 8 + 16))) return r;
-        CK(cudaMemsetAsync(g->bin_mem[1][3], 0, g->bins[0].n_hvert * 4 + 16, st));
-        g->bins[1].hcnt = (uint32_t*)g->bin_mem[1][3];
-        g->bins[1].hpart = (float2*)g->bin_mem[1][4];
-    } else if ((r = build_bins(g, 1, g->csc_off, t1, t2, st))) {
-        return r;
+    ++g->use_clock;
+    for (BinSet* S : g->binsets)
+        if (S->t1 == t1 && S->t2 == t2) {
+            S->last_use = g->use_clock;
+            g->cur = S;
+            return IP_OK;
+        }
+    if (g->binsets.size() >= 4) {  // evict the least recently used set (and the graphs that bake it in)
+        size_t lru = 0;
+        for (size_t i = 1; i < g->binsets.size(); ++i)
+            if (g->binsets[i]->last_use < g->binsets[lru]->last_use) lru = i;
+        free_graph_exec(g);
+        if (g->cur == g->binsets[lru]) g->cur = nullptr;
+        free_binset(g, g->binsets[lru]);
+        g->binsets.erase(g->binsets.begin() + lru);
     }
-    // heavy broadcaster queues hold at most every heavy CSR chunk once
-    for (int p = 0; p < 2; ++p) {
-        if (g->hq[p]) {
-            cudaFree(g->hq[p]);
-            g->device_bytes -= (size_t)(g->hq_cap + 1) * sizeof(uint2);
-            g->hq[p] = nullptr;
+    BinSet* S = new (std::nothrow) BinSet();
+    if (!S) return IP_E_NOMEM;
+    S->t1 = t1;
+    S->t2 = t2;
+    int r = build_bins(g, S, 0, g->csr_off, st);
+    if (!r) {
+        if (g->csc_alias) {
+            // share the CSR bins except the PageRank finish state, which must be private
+            S->b[1] = S->b[0];
+            r = bin_alloc(g, S, 1, 3, S->b[0].n_hvert * 4 + 16);
+            if (!r) r = bin_alloc(g, S, 1, 4, S->b[0].n_hchunk * 8 + 16);
+            if (!r) r = cuda_err(cudaMemsetAsync(S->mem[1][3], 0, S->b[0].n_hvert * 4 + 16, st));
+            S->b[1].hcnt = (uint32_t*)S->mem[1][3];
+            S->b[1].hpart = (float2*)S->mem[1][4];
+        } else {
+            r = build_bins(g, S, 1, g->csc_off, st);
         }
     }
-    g->hq_cap = g->bins[0].n_hchunk;
-    for (int p = 0; p < 2; ++p)
-        if ((r = alloc_dev(g, (void**)&g->hq[p], (size_t)(g->hq_cap + 1) * sizeof(uint2)))) return r;
-    g->bins_t1 = t1;
-    g->bins_t2 = t2;
+    if (!r && S->b[0].n_hchunk > g->hq_cap) {  // heavy broadcaster queues hold every heavy CSR chunk once
+        free_graph_exec(g);
+        for (int p = 0; p < 2; ++p)
+            if (g->hq[p]) {
+                cudaFree(g->hq[p]);
+                g->device_bytes -= (size_t)(g->hq_cap + 1) * sizeof(uint2);
+                g->hq[p] = nullptr;
+            }
+        g->hq_cap = S->b[0].n_hchunk;
+        for (int p = 0; p < 2 && !r; ++p) r = alloc_dev(g, (void**)&g->hq[p], (size_t)(g->hq_cap + 1) * sizeof(uint2));
+    }
+    if (r) {
+        free_binset(g, S);
+        return r;
+    }
+    S->last_use = g->use_clock;
+    g->binsets.push_back(S);
+    g->cur = S;
     return IP_OK;
 }
 
@@ -391,7 +411,9 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
     CK(cudaMemcpyAsync(&g->max_in_deg, mx, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaMemsetAsync(mx, 0, 4, st));
-    g->bins_t1 = g->bins_t2 = 0;
+    if ((r = alloc_dev(g, (void**)&g->hq[0], sizeof(uint2)))) return r;
+    if ((r = alloc_dev(g, (void**)&g->hq[1], sizeof(uint2)))) return r;
+    g->hq_cap = 0;
     if ((r = ensure_bins(g, DEFAULT_T1, DEFAULT_T2, st))) return r;
     CK(cudaEventCreate(&g->ev0));
     CK(cudaEventCreate(&g->ev1));
@@ -432,9 +454,8 @@ void ip_graph_destroy(ip_graph_t* g) {
                     g->q[0][0],    g->q[0][1],    g->q[1][0], g->q[1][1],    g->hq[0],      g->hq[1]};
     for (void* p : bufs)
         if (p) cudaFree(p);
-    for (int k = 0; k < 2; ++k)
-        for (int i = 0; i < 5; ++i)
-            if (g->bin_mem[k][i]) cudaFree(g->bin_mem[k][i]);
+    for (BinSet* S : g->binsets) free_binset(g, S);
+    g->binsets.clear();
     if (!g->csc_alias) {
         if (g->csc_off) cudaFree(g->csc_off);
         if (g->csc_row) cudaFree(g->csc_row);

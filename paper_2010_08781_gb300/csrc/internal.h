@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/ipregel.h"
 
 namespace ipg {
@@ -118,6 +120,23 @@ struct Params {
     cudaGraphConditionalHandle h_while, h_switch;
 };
 
+// Degree bins of both directions for one (t1, t2) pair, with their device buffers.
+struct BinSet {
+    uint32_t t1 = 0, t2 = 0;
+    Bins b[2] = {};  // [0] CSR, [1] CSC
+    void* mem[2][5] = {};
+    size_t bytes[2][5] = {};
+    uint64_t last_use = 0;
+};
+
+// One instantiated superstep graph, keyed by the kernel parameters it bakes in.
+struct ExecEntry {
+    unsigned char key[sizeof(Params)];
+    cudaGraphExec_t exec;
+    cudaGraph_t graph;
+    uint64_t last_use;
+};
+
 }  // namespace ipg
 
 struct ip_graph {
@@ -136,10 +155,8 @@ struct ip_graph {
     bool weighted = false;
     uint32_t max_out_deg = 0, max_in_deg = 0;
     float* inv_outdeg = nullptr;
-    uint32_t bins_t1 = 0, bins_t2 = 0;
-    ipg::Bins bins[2] = {};     // [0] CSR, [1] CSC (aliases [0] for a symmetric graph)
-    void* bin_mem[2][5] = {};  // device buffers behind bins[k]
-    size_t bin_bytes[2][5] = {};
+    std::vector<ipg::BinSet*> binsets;  // degree bins cached by (t1, t2), at most 4
+    ipg::BinSet* cur = nullptr;          // the set of the current run
     // run state
     uint32_t* value = nullptr;
     float* rank = nullptr;
@@ -164,11 +181,9 @@ struct ip_graph {
     // scratch used by label collection (snapshots)
     uint32_t* snap_value = nullptr;
 
-    // cached CUDA graph of the last device-side run
-    cudaGraphExec_t gexec = nullptr;
-    cudaGraph_t graph = nullptr;
-    unsigned char gkey[sizeof(ipg::Params)] = {0};
-    bool has_gkey = false;
+    // instantiated superstep graphs of recent runs, at most 8
+    std::vector<ipg::ExecEntry> execs;
+    uint64_t use_clock = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int grid[16] = {0};
     bool grids_ready = false;

@@ -1044,11 +1044,11 @@ int label_loop(ip_graph* g, const Params& P, cudaStream_t st, ip_run_stats_t* st
 }  // namespace
 
 void free_graph_exec(ip_graph* g) {
-    if (g->gexec) cudaGraphExecDestroy(g->gexec);
-    if (g->graph) cudaGraphDestroy(g->graph);
-    g->gexec = nullptr;
-    g->graph = nullptr;
-    g->has_gkey = false;
+    for (ExecEntry& e : g->execs) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        if (e.graph) cudaGraphDestroy(e.graph);
+    }
+    g->execs.clear();
 }
 
 namespace {
@@ -1075,8 +1075,7 @@ int add_conditional(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphCond
 }
 
 // Whole run as one graph: init, select, then while(continue){ switch(mode){...}; select }.
-int build_graph(ip_graph* g, Params P) {
-    free_graph_exec(g);
+int build_graph(ip_graph* g, Params P, cudaGraphExec_t* exec_out, cudaGraph_t* graph_out) {
     cudaStream_t cap;
     CKR(cuda_err(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)));
     int r = IP_OK;
@@ -1123,15 +1122,44 @@ int build_graph(ip_graph* g, Params P) {
             if (!r) r = cuda_err(e);
         }
     } while (0);
-    if (!r) r = cuda_err(cudaGraphInstantiate(&g->gexec, graph, 0));
+    cudaGraphExec_t exec = nullptr;
+    if (!r) r = cuda_err(cudaGraphInstantiate(&exec, graph, 0));
     cudaStreamDestroy(cap);
     if (r) {
         if (graph) cudaGraphDestroy(graph);
-        g->gexec = nullptr;
         (void)cudaGetLastError();
         return r;
     }
-    g->graph = graph;
+    *exec_out = exec;
+    *graph_out = graph;
+    return IP_OK;
+}
+
+// The instantiated graph for these parameters: cached, least recently used evicted.
+int graph_for(ip_graph* g, const Params& P, cudaGraphExec_t* exec) {
+    Params key = P;
+    key.h_while = key.h_switch = 0;
+    ++g->use_clock;
+    for (ExecEntry& e : g->execs)
+        if (memcmp(e.key, &key, sizeof(Params)) == 0) {
+            e.last_use = g->use_clock;
+            *exec = e.exec;
+            return IP_OK;
+        }
+    if (g->execs.size() >= 8) {
+        size_t lru = 0;
+        for (size_t i = 1; i < g->execs.size(); ++i)
+            if (g->execs[i].last_use < g->execs[lru].last_use) lru = i;
+        cudaGraphExecDestroy(g->execs[lru].exec);
+        cudaGraphDestroy(g->execs[lru].graph);
+        g->execs.erase(g->execs.begin() + lru);
+    }
+    ExecEntry e;
+    memcpy(e.key, &key, sizeof(Params));
+    CKR(build_graph(g, P, &e.exec, &e.graph));
+    e.last_use = g->use_clock;
+    g->execs.push_back(e);
+    *exec = e.exec;
     return IP_OK;
 }
 
@@ -1157,10 +1185,7 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     const uint32_t t1 = o.t1 ? o.t1 : DEFAULT_T1;
     const uint32_t t2 = o.t2 ? o.t2 : DEFAULT_T2;
     if (t1 >= t2) return IP_E_INVAL;
-    if (g->bins_t1 != t1 || g->bins_t2 != t2) {
-        free_graph_exec(g);
-        CKR(ensure_bins(g, t1, t2, st));
-    }
+    CKR(ensure_bins(g, t1, t2, st));
     compute_grids(g);
 
     const uint32_t want_log = std::min<uint32_t>(max_supersteps, 1u << 16);
@@ -1187,8 +1212,8 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     P.csc_off = g->csc_off;
     P.csc_row = g->csc_row;
     P.csc_w = g->csc_w;
-    P.bout = g->bins[0];
-    P.bin = g->bins[1];
+    P.bout = g->cur->b[0];
+    P.bin = g->cur->b[1];
     P.inv_outdeg = g->inv_outdeg;
     P.value = g->value;
     P.rank = g->rank;
@@ -1243,16 +1268,10 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     if (o.collect_labels) {
         r = label_loop(g, P, st, stats);
     } else if (use_graph) {
-        // the graph bakes the kernel parameters; rebuild when they change
-        Params key = P;
-        key.h_while = key.h_switch = 0;
-        if (!g->has_gkey || memcmp(g->gkey, &key, sizeof(Params)) != 0 || !g->gexec) {
-            r = build_graph(g, P);
-            if (r) return r;
-            memcpy(g->gkey, &key, sizeof(Params));
-            g->has_gkey = true;
-        }
-        r = cuda_err(cudaGraphLaunch(g->gexec, st));
+        // the graph bakes the kernel parameters: one instantiated graph per parameter set
+        cudaGraphExec_t exec = nullptr;
+        r = graph_for(g, P, &exec);
+        if (!r) r = cuda_err(cudaGraphLaunch(exec, st));
     } else {
         r = host_loop(g, P, st, o.profile_kernels != 0, stats);
     }

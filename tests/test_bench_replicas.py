@@ -1,0 +1,57 @@
+"""bench.py's multi-GPU path is replicas only: each rank runs its own workload and
+the whole-job rate is (messages of all ranks) / (slowest rank's time). The host
+logic is checked here with two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t, m = bench.reduce_over_ranks(10.0 + 5 * rank, 1000 * (rank + 1), world, "cpu")
+    out.put((rank, t, m))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_reduction_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for _, t, m in res:
+        assert t == 15.0 and m == 3000.0  # slowest rank's time, all ranks' messages
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.reduce_over_ranks(7.5, 42, 1) == (7.5, 42.0)
+
+
+def test_reference_arm_prints_one_line(capsys, monkeypatch):
+    """--impl reference times the CPU oracle; a tiny scale keeps this a unit test."""
+    import sys
+    import json
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                                      "--scale", "10"])
+    bench.main()
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
