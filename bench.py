@@ -332,8 +332,12 @@ def ncu_case(spec, scale):
     profile kernels inside graphs with conditional nodes), run twice; or
     batch_sssp:K — K sources at once in the persistent kernel."""
     import paper_2010_08781_gb300 as ipg
-    app, mode = spec.split(":")
-    g = build_graph(scale)
+    app, mode, *rest = spec.split(":")
+    if app == "pagerank":  # directed R-MAT, as the PageRank configurations use
+        import inputs
+        g = inputs.rmat_graph(scale, edge_factor=EDGE_FACTOR, a=0.57, b=0.19, c=0.19, seed=1)
+    else:
+        g = build_graph(scale)
     if app == "batch_sssp":
         import inputs
         k = int(mode)
@@ -347,6 +351,8 @@ def ncu_case(spec, scale):
     with ipg.Graph.from_inputs(g) as G:
         for _ in range(2):
             kw = dict(policy="forced", forced_mode=mode) if app != "pagerank" or mode != "auto" else {}
+            if rest:  # PageRank pull engine: gather or blocked
+                kw["pr_engine"] = rest[0]
             st = G.run(app, use_graph=0, **kw)
     print(json.dumps({"ncu_case": spec, "scale": scale, "edges": g.m, "supersteps": st.supersteps,
                       "ms": round(st.elapsed_ms, 4)}))
@@ -439,7 +445,8 @@ def main():
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--policy", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ncu-case", default=None, help="APP:MODE, e.g. sssp:pull — small profiling case only")
+    ap.add_argument("--ncu-case", default=None,
+                    help="APP:MODE[:ENGINE], e.g. sssp:pull or pagerank:pull:blocked — small profiling case only")
     ap.add_argument("--config", default=None, choices=["c1", "c4", "c5"],
                     help="secondary configurations: c1 PageRank scale 16, c4 batched, c5 scale 26")
     args = ap.parse_args()

@@ -70,6 +70,18 @@ typedef enum {
     IP_POLICY_SEQUENCE = 4   /* exchange into superstep s uses mode_sequence[(s-1) % len] */
 } ip_policy_t;
 
+/* How PageRank runs a PULL exchange. Both compute the same sums; they differ in
+ * how the in-neighbours' broadcasts reach the destination. */
+typedef enum {
+    IP_PR_ENGINE_AUTO = 0,    /* BLOCKED on graphs of at least 2^24 edges that it supports, else GATHER */
+    IP_PR_ENGINE_GATHER = 1,  /* every in-edge of the CSC reads its source's broadcast */
+    IP_PR_ENGINE_BLOCKED = 2  /* two streaming passes over a second edge layout built on first use
+                                 (8 bytes per edge): the sources' broadcasts are written out per
+                                 edge, grouped by destination bin, and every bin is summed in shared
+                                 memory in 64-bit fixed point; IP_E_RANGE on graphs of more than
+                                 339,738,624 vertices */
+} ip_pr_engine_t;
+
 typedef struct ip_graph ip_graph_t;
 
 /* Options of one run. Fill with ip_options_default() and override fields. */
@@ -95,6 +107,7 @@ typedef struct {
     int32_t profile_kernels;      /* 1: host loop with CUDA events around every kernel; fills
                                      ip_run_stats_t.kernel_ms. Values are unchanged. */
     void* stream;                 /* cudaStream_t */
+    int32_t pr_engine;            /* ip_pr_engine_t (default IP_PR_ENGINE_AUTO) */
 } ip_options_t;
 
 /* Per-run statistics. The caller owns the arrays; `capacity` is their length in

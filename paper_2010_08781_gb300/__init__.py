@@ -29,6 +29,7 @@ PAGERANK, HASHMIN, SSSP = 0, 1, 2
 APPS = {"pagerank": PAGERANK, "hashmin": HASHMIN, "sssp": SSSP}
 PUSH_SPARSE, PUSH_DENSE, PULL = 0, 1, 2
 MODES = {"push_sparse": PUSH_SPARSE, "push_dense": PUSH_DENSE, "pull": PULL}
+PR_ENGINES = {"auto": 0, "gather": 1, "blocked": 2}
 POLICY_AUTO, POLICY_THRESHOLD, POLICY_MLP, POLICY_FORCED, POLICY_SEQUENCE = 0, 1, 2, 3, 4
 SELECTOR_BYTES = 16 * 4 + (32 * 8 + 32 * 32 + 3 * 32) * 2 + (32 + 32 + 3) * 4
 N_FEATURES = 8
@@ -49,7 +50,7 @@ class Options(ctypes.Structure):
                 ("mode_sequence", ctypes.POINTER(ctypes.c_uint8)), ("mode_sequence_len", ctypes.c_uint32),
                 ("t1", ctypes.c_uint32), ("t2", ctypes.c_uint32), ("thr_sparse", ctypes.c_float),
                 ("thr_pull", ctypes.c_float), ("use_graph", ctypes.c_int32), ("collect_labels", ctypes.c_int32),
-                ("profile_kernels", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("profile_kernels", ctypes.c_int32), ("stream", ctypes.c_void_p), ("pr_engine", ctypes.c_int32)]
 
 
 class RunStatsC(ctypes.Structure):
@@ -194,6 +195,8 @@ def default_options(app=None, **kw) -> Options:
                  "sequence": POLICY_SEQUENCE}[v]
         if k == "forced_mode" and isinstance(v, str):
             v = MODES[v]
+        if k == "pr_engine" and isinstance(v, str):
+            v = PR_ENGINES[v]
         if k == "stream" and v is not None and not isinstance(v, int):
             v = v.cuda_stream  # torch.cuda.Stream
         setattr(o, k, v)

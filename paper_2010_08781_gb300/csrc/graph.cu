@@ -442,12 +442,14 @@ void ip_options_default(ip_options_t* o) {
     o->use_graph = 1;
     o->collect_labels = 0;
     o->stream = nullptr;
+    o->pr_engine = IP_PR_ENGINE_AUTO;
 }
 
 void ip_graph_destroy(ip_graph_t* g) {
     if (!g) return;
     free_graph_exec(g);
     free_batch_state(g);
+    pb_free(g);
     void* bufs[] = {g->ctl,        g->csr_off,    g->csr_col, g->csr_w,      g->inv_outdeg, g->value,
                     g->rank,       g->contrib[0], g->contrib[1], g->mbox,  g->mboxf,      g->recv, g->outbox,
                     g->bcast[0],   g->bcast[1],   g->rq,      g->log,        g->sel,        g->snap_value,

@@ -76,6 +76,30 @@ struct Bins {
     float2* hpart;        // per chunk: compensated partial sum (PageRank)
 };
 
+// Blocked PageRank pull (pb.cu): the edges are stored once more, grouped by
+// source chunk and, inside a chunk, by destination bin. Phase 1 streams every
+// chunk and writes its sources' broadcasts next to the entries; phase 2
+// accumulates every bin in shared memory. Device pointers of that layout.
+constexpr uint32_t PB_BIN_V = 24576;  // most destinations per bin (one 32-bit accumulator word each in shared memory)
+constexpr uint64_t PB_AUTO_EDGES = 1ull << 24;  // IP_PR_ENGINE_AUTO picks the blocked pull from this many edges
+struct PbDev {
+    uint32_t on;             // 1: PageRank pull runs on this layout
+    uint32_t n_chunks, n_tasks;
+    const uint2* chunk;      // [n_chunks] {first source, source count}
+    const uint32_t* pbase;   // [n_chunks + 1] first entry of each chunk (multiples of 8)
+    const uint32_t* corder;  // chunks by decreasing entry count
+    const uint16_t* src;     // [entries] source minus the first source of its chunk (padding: the count)
+    const uint16_t* dst;     // [entries] destination minus the first vertex of its bin
+    uint32_t* code;          // [entries] broadcast of the entry's source as a fixed-point code (phase 1)
+    unsigned long long* big; // [V] fixed-point broadcasts of 2^31 units or more (code = 2^31 | source)
+    const uint32_t* units;   // per bin, the units (8 aligned entries) of its runs: entry index / 8
+    const uint4* tasks;      // per bin {first vertex, vertices, first unit, end unit}, in bin order
+    uint32_t* hi;            // [V] high words of the fixed-point sums, zero between launches
+    uint32_t* ctr;           // [2] task counters of phase 1 and phase 2
+    int32_t shift;           // S: a contribution v is added as round(v * 2^S)
+    float inv_scale;         // 2^-S
+};
+
 // Everything a superstep kernel needs, passed by value.
 struct Params {
     uint32_t V;
@@ -118,7 +142,16 @@ struct Params {
     uint32_t out_deg_src;
     int32_t use_graph;
     cudaGraphConditionalHandle h_while, h_switch;
+    PbDev pb;
 };
+
+// PageRank compute() of superstep s (Fig. 8): rank from the sum of the received
+// broadcasts, then broadcast rank / out-degree while s < T.
+__device__ __forceinline__ void pr_finish(const Params& P, uint32_t v, float sum, uint32_t s, float* nxt) {
+    const float r = fmaf(P.damping, sum, P.pr_base);  // (1-d)/N + d * sum
+    P.rank[v] = r;
+    nxt[v] = s < P.T ? r * P.inv_outdeg[v] : 0.0f;
+}
 
 // Degree bins of both directions for one (t1, t2) pair, with their device buffers.
 struct BinSet {
@@ -189,6 +222,7 @@ struct ip_graph {
     bool grids_ready = false;
     void* batch = nullptr;        // state of the batched runs (batch.cu)
     uint32_t* track_send = nullptr;  // when set, runs record per-vertex last sends here (batched Hashmin)
+    void* pb = nullptr;              // blocked PageRank pull layout (pb.cu), built on first use
 };
 
 namespace ipg {
@@ -198,6 +232,11 @@ int ensure_bins(ip_graph* g, uint32_t t1, uint32_t t2, cudaStream_t st);
 int cuda_err(cudaError_t e);
 // batch.cu
 void free_batch_state(ip_graph* g);
+// pb.cu
+int pb_prepare(ip_graph* g, cudaStream_t st, PbDev* out);
+int pb_launch(const ip_graph* g, const Params& P, cudaStream_t st);
+bool pb_supported(const ip_graph* g);
+void pb_free(ip_graph* g);
 // superstep.cu
 int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* opt, ip_run_stats_t* stats);
 void free_graph_exec(ip_graph* g);

@@ -229,6 +229,7 @@ __global__ void k_pr_init(Params P) {
         P.contrib0[v] = P.T > 0 ? r0 * P.inv_outdeg[v] : 0.0f;
         P.mboxf[v] = 0.0f;
     }
+    if (P.pb.on && tid == 0) P.pb.ctr[0] = P.pb.ctr[1] = 0;
     if (tid == 0) {
         DevCtl* c = P.ctl;
         c->superstep = 0;
@@ -596,12 +597,6 @@ __global__ void __launch_bounds__(BLOCK) k_apply_queue(Params P) {
 }
 
 // ================================================================ PageRank
-__device__ __forceinline__ void pr_finish(const Params& P, uint32_t v, float sum, uint32_t s, float* nxt) {
-    const float r = fmaf(P.damping, sum, P.pr_base);  // (1-d)/N + d * sum
-    P.rank[v] = r;
-    nxt[v] = s < P.T ? r * P.inv_outdeg[v] : 0.0f;  // broadcast value/out-degree while s < T
-}
-
 // Compensated sum of cur[u] over the in-edges [b, e); thread pos of a group of
 // `stride` threads takes blocks pos, pos+stride, ...
 __device__ __forceinline__ void pr_gather(const uint32_t* row, const float* cur, uint32_t b, uint32_t e, uint32_t pos,
@@ -896,7 +891,12 @@ int launch_superstep(const ip_graph* g, const Params& P, int mode, cudaStream_t 
     if (P.app == APP_PR) {
         mark(1);
         if (mode == IP_MODE_PULL) {
-            k_pr_pull<<<G[G_PR_PULL], BLOCK, 0, st>>>(P);
+            if (P.pb.on) {
+                const int r = pb_launch(g, P, st);
+                if (r != IP_OK) return r;
+            } else {
+                k_pr_pull<<<G[G_PR_PULL], BLOCK, 0, st>>>(P);
+            }
             mark(2);
         } else {
             k_pr_push<<<G[G_PR_PUSH], BLOCK, 0, st>>>(P);
@@ -1182,6 +1182,7 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     }
     if (o.policy == IP_POLICY_MLP && !g->has_selector) return IP_E_STATE;
     if (app == APP_PR && !(o.damping >= 0.f && o.damping <= 1.f)) return IP_E_INVAL;
+    if (o.pr_engine < IP_PR_ENGINE_AUTO || o.pr_engine > IP_PR_ENGINE_BLOCKED) return IP_E_INVAL;
     const uint32_t t1 = o.t1 ? o.t1 : DEFAULT_T1;
     const uint32_t t2 = o.t2 ? o.t2 : DEFAULT_T2;
     if (t1 >= t2) return IP_E_INVAL;
@@ -1259,6 +1260,15 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     }
     const bool use_graph = o.use_graph && !o.collect_labels && !o.profile_kernels;
     P.use_graph = use_graph ? 1 : 0;
+    if (app == APP_PR) {
+        const bool blocked = o.pr_engine == IP_PR_ENGINE_BLOCKED ||
+                             (o.pr_engine == IP_PR_ENGINE_AUTO && g->E >= PB_AUTO_EDGES && pb_supported(g));
+        if (blocked) {
+            const int r = pb_prepare(g, st, &P.pb);
+            // AUTO keeps the gather engine where the layout does not fit (entries beyond 2^32)
+            if (r != IP_OK && !(r == IP_E_RANGE && o.pr_engine == IP_PR_ENGINE_AUTO)) return r;
+        }
+    }
 
     if (stats && stats->mode_ms && stats->capacity) memset(stats->mode_ms, 0, sizeof(float) * 3 * stats->capacity);
     if (stats && stats->kernel_ms && stats->capacity)
