@@ -85,15 +85,14 @@ constexpr uint64_t PB_AUTO_EDGES = 1ull << 24;  // IP_PR_ENGINE_AUTO picks the b
 struct PbDev {
     uint32_t on;             // 1: PageRank pull runs on this layout
     uint32_t n_chunks, n_tasks;
-    const uint2* chunk;      // [n_chunks] {first source, source count}
-    const uint32_t* pbase;   // [n_chunks + 1] first entry of each chunk (multiples of 8)
-    const uint32_t* corder;  // chunks by decreasing entry count
-    const uint16_t* src;     // [entries] source minus the first source of its chunk (padding: the count)
-    const uint16_t* dst;     // [entries] destination minus the first vertex of its bin
-    uint32_t* code;          // [entries] broadcast of the entry's source as a fixed-point code (phase 1)
+    const uint4* chunk;      // [n_chunks] {first source, sources, first run, end run}
+    const uint4* runs;       // {chunk-major first entry, bin-major first entry, length padded to 4, 0},
+                             // by chunk then bin
+    const uint16_t* src;     // chunk-major: source minus the first source of its chunk (padding: source count)
+    const uint16_t* dst;     // [entries] bin-major: destination minus the first vertex of its bin (padding 0)
+    uint32_t* code;          // [entries] bin-major: the source's broadcast as a fixed-point code (padding 0)
     unsigned long long* big; // [V] fixed-point broadcasts of 2^31 units or more (code = 2^31 | source)
-    const uint32_t* units;   // per bin, the units (8 aligned entries) of its runs: entry index / 8
-    const uint4* tasks;      // per bin {first vertex, vertices, first unit, end unit}, in bin order
+    const uint4* tasks;      // per bin {first vertex, vertices, first entry, end entry}, in bin order
     uint32_t* hi;            // [V] high words of the fixed-point sums, zero between launches
     uint32_t* ctr;           // [2] task counters of phase 1 and phase 2
     int32_t shift;           // S: a contribution v is added as round(v * 2^S)

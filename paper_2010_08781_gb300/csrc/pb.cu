@@ -12,15 +12,20 @@
 //   consecutive sources (at most PB_MAXS sources, about PB_CHUNK_E edges), the
 //   vertices into bins of consecutive destinations (at most PB_BIN_V vertices and
 //   about E / (4 x phase-2 CTAs) in-edges, so that every bin is a balanced task).
-//   Inside a chunk the entries are grouped by bin; entry i stores its source
-//   relative to the chunk (u16) and its destination relative to the bin (u16).
-//   A run is the entries of one chunk into one bin, padded to whole units of 8
-//   entries whose broadcast is 0; every bin lists the units of its runs.
+//   A run is the edges of one chunk into one bin, padded to a multiple of 4
+//   entries (padding adds 0). Every entry is stored twice: its source relative
+//   to the chunk (u16) in chunk-major order (chunk, then bin), its destination
+//   relative to the bin (u16) and its code in bin-major order (bin, then chunk).
+//   A run is contiguous in both orders.
 //   phase 1 (k_pb_scatter): a CTA stages its chunk's broadcasts in shared
-//   memory, as fixed-point codes, and writes code[i] = code of src[i], streaming.
-//   phase 2 (k_pb_accumulate): a CTA owns one bin, reads that bin's units and
-//   adds every code into a shared-memory accumulator of its destination, then
-//   runs compute() (pr_finish) for the bin's vertices.
+//   memory as fixed-point codes, then copies every run: sources read in order,
+//   codes written to the run's place in its bin. Chunks go in index order, so
+//   the runs of neighbouring chunks (neighbours in every bin) are written close
+//   in time and their shared sectors meet in L2.
+//   phase 2 (k_pb_accumulate): a CTA owns one bin, streams its codes and
+//   destinations through asynchronous copies into shared memory and adds every
+//   code into a shared-memory accumulator of its destination, then runs
+//   compute() (pr_finish) for the bin's vertices.
 //
 // The accumulators are 64-bit fixed point (2^-S units: the low 32-bit word in
 // shared memory, the high word in global memory, an explicit carry between
@@ -44,11 +49,16 @@ constexpr uint32_t PB_MAXS = 16384;      // sources per chunk: their codes fit 6
 constexpr uint32_t PB_CHUNK_E = 131072;  // target out-edges per chunk
 constexpr uint32_t PB_MAX_BINS = 16384;  // bins a chunk histograms in shared memory
 constexpr uint32_t PB_MAX_V = 13824u * PB_BIN_V;  // vertex-capped bins plus entry-capped ones fit PB_MAX_BINS
-constexpr int PB1_THREADS = 512, PB2_THREADS = 512, PBB_THREADS = 512;
-constexpr int PB1_LOADS = 4;  // phase 1: 16-byte loads per thread in flight
-constexpr int PB_U = 4;       // phase 2: groups of 64 entries (2 per lane) per claim of 32 units
+constexpr int PB1_THREADS = 512, PBB_THREADS = 512;
+constexpr int PB1_LOADS = 4;         // phase 1: groups of 4 entries per lane in flight
+constexpr int PB_BATCH = 8;          // per-vertex loops (staging, compute()): loads in flight per thread
+constexpr int PB2_CONSUMERS = 16;    // phase 2: consumer warps (plus one producer warp)
+constexpr int PB_GROUPS = 2;        // phase 2: groups of 4 entries per consumer thread and stage
+constexpr uint32_t PB_TILE = 4 * PB_GROUPS * 32 * PB2_CONSUMERS;  // entries per stage (4096)
+constexpr int PB_STAGES = 5;         // phase 2: stages of the bulk-copy ring (120 KB)
 constexpr size_t PB1_SMEM = (PB_MAXS + 1) * sizeof(uint32_t);
-constexpr size_t PB2_SMEM = PB_BIN_V * sizeof(uint32_t);
+constexpr size_t PB2_SMEM = PB_BIN_V * sizeof(uint32_t) + (size_t)PB_STAGES * PB_TILE * (4 + 2) +
+                            PB_STAGES * (32 + 16);
 
 // v * 2^S as a 64-bit integer (xl, xh), rounded half up, from the bits of v
 // (0 <= v < 2, S <= 62: the product stays below 2^63). Integer arithmetic only:
@@ -71,52 +81,91 @@ __device__ __forceinline__ void pb_fixed(float v, int S, uint32_t& xl, uint32_t&
 // ---------------------------------------------------------------- phase 1
 // Staging turns every source's broadcast into its 32-bit code once: the
 // fixed-point value itself below 2^31, else 2^31 | source with the 64-bit value
-// in big[source]. The entries then only copy codes.
+// in big[source]. Then every warp copies whole runs, lane by lane.
 __global__ void __launch_bounds__(PB1_THREADS) k_pb_scatter(Params P) {
     extern __shared__ uint32_t scode[];
-    __shared__ uint32_t task;
+    __shared__ uint32_t task, next_win;
     const PbDev& B = P.pb;
     const uint32_t s = P.ctl->superstep;  // the superstep being computed
     const float* cur = (s & 1) ? P.contrib0 : P.contrib1;
+    const uint32_t lane = threadIdx.x & 31;
     if (blockIdx.x == 0 && threadIdx.x == 0) B.ctr[1] = 0;  // phase 2 of this superstep claims from 0
     for (;;) {
         if (threadIdx.x == 0) task = atomicAdd(B.ctr, 1u);
         __syncthreads();
-        const uint32_t t = task;
-        if (t >= B.n_chunks) break;
-        const uint32_t c = B.corder[t];
-        const uint32_t s0 = B.chunk[c].x, ns = B.chunk[c].y;
-        for (uint32_t i = threadIdx.x; i < ns; i += blockDim.x) {
-            uint32_t xl, xh;
-            pb_fixed(cur[s0 + i], B.shift, xl, xh);
-            uint32_t code = xl;
-            if (xh || xl >= 0x80000000u) {
-                code = 0x80000000u | (s0 + i);
-                B.big[s0 + i] = ((unsigned long long)xh << 32) | xl;
-            }
-            scode[i] = code;
-        }
-        if (threadIdx.x == 0) scode[ns] = 0u;  // source of the padding entries
-        __syncthreads();
-        const uint32_t p8 = B.pbase[c] >> 3, n8 = (B.pbase[c + 1] >> 3) - p8;
-        const uint4* src8 = reinterpret_cast<const uint4*>(B.src) + p8;
-        uint4* code4 = reinterpret_cast<uint4*>(B.code) + 2 * (size_t)p8;
-        for (uint32_t j0 = threadIdx.x; j0 < n8; j0 += PB1_LOADS * blockDim.x) {
-            uint4 a[PB1_LOADS];
+        const uint32_t c = task;
+        if (c >= B.n_chunks) break;
+        const uint4 ch = B.chunk[c];  // {first source, sources, first run, end run}
+        const uint32_t s0 = ch.x, ns = ch.y;
+        for (uint32_t i0 = threadIdx.x; i0 < ns; i0 += PB_BATCH * blockDim.x) {  // PB_BATCH loads in flight
+            float x[PB_BATCH];
 #pragma unroll
-            for (int k = 0; k < PB1_LOADS; ++k) {
-                const uint32_t j = j0 + k * blockDim.x;
-                a[k] = j < n8 ? __ldcs(src8 + j) : make_uint4(0, 0, 0, 0);
+            for (int u = 0; u < PB_BATCH; ++u) {
+                const uint32_t i = i0 + u * blockDim.x;
+                x[u] = i < ns ? cur[s0 + i] : 0.0f;
             }
 #pragma unroll
-            for (int k = 0; k < PB1_LOADS; ++k) {
-                const uint32_t j = j0 + k * blockDim.x;
-                if (j < n8) {
-                    code4[2 * j] = make_uint4(scode[a[k].x & 0xFFFF], scode[a[k].x >> 16], scode[a[k].y & 0xFFFF],
-                                              scode[a[k].y >> 16]);
-                    code4[2 * j + 1] = make_uint4(scode[a[k].z & 0xFFFF], scode[a[k].z >> 16],
-                                                  scode[a[k].w & 0xFFFF], scode[a[k].w >> 16]);
+            for (int u = 0; u < PB_BATCH; ++u) {
+                const uint32_t i = i0 + u * blockDim.x;
+                if (i < ns) {
+                    uint32_t xl, xh;
+                    pb_fixed(x[u], B.shift, xl, xh);
+                    uint32_t code = xl;
+                    if (xh || xl >= 0x80000000u) {
+                        code = 0x80000000u | (s0 + i);
+                        B.big[s0 + i] = ((unsigned long long)xh << 32) | xl;
+                    }
+                    scode[i] = code;
                 }
+            }
+        }
+        if (threadIdx.x == 0) {
+            scode[ns] = 0u;  // source of the padding entries
+            next_win = 0;
+        }
+        __syncthreads();
+        // a warp takes windows of 32 consecutive runs (lengths padded to 4 entries);
+        // their sources are one contiguous chunk-major range, so lane k of a step
+        // reads the 4 entries a0 + 4k.. and finds their run (for the bin-major
+        // place) by a search over the window
+        const uint32_t nwin = (ch.w - ch.z + 31) / 32;
+        for (;;) {  // windows are claimed one by one: their sizes vary
+            uint32_t wi = 0;
+            if (lane == 0) wi = atomicAdd(&next_win, 1u);
+            wi = __shfl_sync(FULL, wi, 0);
+            if (wi >= nwin) break;
+            const uint32_t r = ch.z + 32 * wi + lane;
+            const uint4 run = r < ch.w ? __ldcs(B.runs + r) : make_uint4(0, 0, 0, 0);
+            const uint32_t a0 = __shfl_sync(FULL, run.x, 0);
+            uint32_t inc = run.z >> 2;  // inclusive prefix of the runs' groups of 4
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, inc, o);
+                if (lane >= (uint32_t)o) inc += y;
+            }
+            const uint32_t total = __shfl_sync(FULL, inc, 31);
+            const uint32_t delta = run.y - run.x;  // bin-major minus chunk-major place (mod 2^32)
+            for (uint32_t k0 = 0; k0 < total; k0 += 32u * PB1_LOADS) {
+                uint2 sv[PB1_LOADS];
+                uint32_t out[PB1_LOADS];
+#pragma unroll
+                for (int u = 0; u < PB1_LOADS; ++u) {
+                    const uint32_t k = k0 + 32u * u + lane;
+                    uint32_t j = 0;  // run of group k: the runs that end at or before it
+#pragma unroll
+                    for (uint32_t st = 16; st; st >>= 1) {
+                        const uint32_t y = __shfl_sync(FULL, inc, j + st - 1);
+                        if (y <= k) j += st;
+                    }
+                    out[u] = __shfl_sync(FULL, delta, j) + a0 + 4 * k;
+                    sv[u] = k < total ? __ldcs(reinterpret_cast<const uint2*>(B.src + a0 + 4 * k)) : make_uint2(0, 0);
+                }
+#pragma unroll
+                for (int u = 0; u < PB1_LOADS; ++u)
+                    if (k0 + 32u * u + lane < total)
+                        *reinterpret_cast<uint4*>(B.code + out[u]) =
+                            make_uint4(scode[sv[u].x & 0xFFFF], scode[sv[u].x >> 16], scode[sv[u].y & 0xFFFF],
+                                       scode[sv[u].y >> 16]);
             }
         }
         __syncthreads();
@@ -142,114 +191,227 @@ __device__ __forceinline__ float pb_value(uint32_t hi, uint32_t lo, float inv_sc
     return fmaf(__uint2float_rn(hi), 4294967296.0f, __uint2float_rn(lo)) * inv_scale;
 }
 
-// One claim of a warp: 32 units (256 entries); lane l holds the index of unit
-// l. In group g lane l takes entries 2(l % 4) and 2(l % 4) + 1 of unit
-// 8g + l / 4, so the four lanes of a unit read one aligned 32-byte sector of
-// codes.
-struct PbClaim {
-    uint2 c[PB_U];
-    uint32_t d[PB_U];
-};
+// ---- mbarrier / bulk-copy helpers (shared-memory addresses are 32-bit)
+__device__ __forceinline__ uint32_t pb_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void pb_load(const PbDev& B, uint32_t u, uint32_t my, uint32_t ue, uint32_t lane,
-                                        PbClaim& x) {
-#pragma unroll
-    for (int g = 0; g < PB_U; ++g) {
-        const uint32_t k = 8 * g + (lane >> 2);
-        const uint32_t unit = __shfl_sync(FULL, my, k);
-        const bool ok = u + k < ue;
-        const uint32_t pos = unit * 8 + 2 * (lane & 3);
-        x.c[g] = ok ? __ldcs(reinterpret_cast<const uint2*>(B.code + pos)) : make_uint2(0, 0);
-        x.d[g] = ok ? __ldcs(reinterpret_cast<const uint32_t*>(B.dst + pos)) : 0u;
+__device__ __forceinline__ void pb_mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void pb_mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void pb_mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void pb_bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t pb_clock_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of the given parity; false after PB_WAIT_NS without it.
+constexpr uint64_t PB_WAIT_NS = 2000000000ull;
+__device__ __forceinline__ bool pb_mbar_wait(uint32_t bar, uint32_t parity) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255u) == 0) {
+            const uint64_t now = pb_clock_ns();
+            if (it == 0)
+                t0 = now;
+            else if (now - t0 > PB_WAIT_NS)
+                return false;
+        }
     }
 }
 
-// Adds one claim: branch free for codes below 2^31 (their own value); carries
-// into the high words and big contributions take a warp-uniform slow path that
-// reads the flagged entries again.
-__device__ __forceinline__ void pb_accumulate_claim(const PbDev& B, uint32_t* acc_lo, uint32_t* hi,
-                                                    const PbClaim& x, uint32_t my, uint32_t lane) {
-    uint32_t carry = 0, bigs = 0;
+// compute() of the bin's vertices first, first + stride, ... < nv (vertex v0 + v):
+// the sum is hi:lo in 2^-S units. PB_BATCH vertices' loads are in flight at once.
+// Clears the vertex's high word and low word for the next bin.
+__device__ __forceinline__ void pb_finish(const Params& P, uint32_t* hi, uint32_t* lo, uint32_t v0, uint32_t nv,
+                                          uint32_t first, uint32_t stride, uint32_t s, float* nxt,
+                                          float inv_scale) {
+    for (uint32_t b = first; b < nv; b += PB_BATCH * stride) {
+        uint32_t h[PB_BATCH];
+        float iod[PB_BATCH];
 #pragma unroll
-    for (int g = 0; g < PB_U; ++g) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t code = h ? x.c[g].y : x.c[g].x;
-            const uint32_t big = code >> 31;
-            const uint32_t v = big ? 0u : code;
-            const uint32_t old = atomicAdd(acc_lo + ((x.d[g] >> (16 * h)) & 0xFFFFu), v);
-            carry |= (old + v < old ? 1u : 0u) << (2 * g + h);
-            bigs |= big << (2 * g + h);
+        for (int u = 0; u < PB_BATCH; ++u) {
+            const uint32_t v = b + u * stride;
+            h[u] = v < nv ? __ldcg(hi + v) : 0u;
+            iod[u] = v < nv ? __ldg(P.inv_outdeg + v0 + v) : 0.0f;
         }
-    }
-    if (__any_sync(FULL, carry | bigs)) {
-        for (int g = 0; g < PB_U; ++g) {
-            const uint32_t unit = __shfl_sync(FULL, my, 8 * g + (lane >> 2));
-            const uint32_t pos = unit * 8 + 2 * (lane & 3);
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t bit = 2 * g + h;
-                if (((carry | bigs) >> bit) & 1u) {
-                    const uint32_t d = B.dst[pos + h];
-                    if ((carry >> bit) & 1u) atomicAdd(hi + d, 1u);
-                    if ((bigs >> bit) & 1u) pb_add_big(B, acc_lo, hi, d, B.code[pos + h]);
-                }
+#pragma unroll
+        for (int u = 0; u < PB_BATCH; ++u) {
+            const uint32_t v = b + u * stride;
+            if (v < nv) {
+                if (h[u]) hi[v] = 0;
+                const float r = fmaf(P.damping, pb_value(h[u], lo[v], inv_scale), P.pr_base);  // as pr_finish
+                P.rank[v0 + v] = r;
+                nxt[v0 + v] = s < P.T ? r * iod[u] : 0.0f;
+                lo[v] = 0;
             }
         }
     }
 }
 
-// Warps claim 32 units at a time from the bin's unit list. Software pipeline:
-// the unit indices of claim n+2 and the codes of claim n+1 are in flight while
-// claim n is added.
-__global__ void __launch_bounds__(PB2_THREADS, 2) k_pb_accumulate(Params P) {
-    extern __shared__ uint32_t acc_lo[];
-    __shared__ uint32_t task, next_unit;
+// Barrier of the consumer warps on an mbarrier of count PB2_CONSUMERS: lane 0
+// of every warp arrives after __syncwarp (ordering its warp's memory operations
+// before the release) and waits, bounded, for the given phase.
+__device__ __forceinline__ bool pb_consumer_sync(uint32_t bar, uint32_t parity, uint32_t lane) {
+    __syncwarp();
+    bool ok = true;
+    if (lane == 0) {
+        pb_mbar_arrive(bar);
+        ok = pb_mbar_wait(bar, parity);
+    }
+    return __shfl_sync(FULL, ok ? 1u : 0u, 0) != 0;
+}
+
+// Phase 2. Warp 0 is the producer: one thread claims bins and streams each
+// bin's codes and destinations in tiles of PB_TILE entries with bulk copies
+// into a ring of PB_STAGES shared-memory stages (full/empty mbarriers). The
+// PB2_CONSUMERS other warps take the tiles in order: thread c adds the groups of
+// 4 entries c, c + 512, ... of a tile (codes below 2^31 branch free; carries into the high words
+// and big contributions in a warp-uniform slow path), and after a bin's last
+// tile they run compute() for its vertices. Every wait (stages, and the
+// consumers' own barriers, which are mbarriers too) is bounded: on timeout a
+// thread records bit 2 in ctl->err (IP_E_TIMEOUT) and stops; the producer then
+// waits, bounded, for its copies in flight.
+__global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(Params P) {
+    extern __shared__ __align__(128) uint32_t acc_lo[];                         // [PB_BIN_V]
+    uint32_t* ring_code = acc_lo + PB_BIN_V;                                    // [PB_STAGES][PB_TILE]
+    uint16_t* ring_dst = reinterpret_cast<uint16_t*>(ring_code + PB_STAGES * PB_TILE);  // [PB_STAGES][PB_TILE]
+    uint4* meta = reinterpret_cast<uint4*>(ring_dst + PB_STAGES * PB_TILE);     // [PB_STAGES][2]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(meta + 2 * PB_STAGES);         // full[PB_STAGES], empty[PB_STAGES]
+    __shared__ __align__(8) uint64_t cbar[2];                                  // consumer barriers
     const PbDev& B = P.pb;
     const uint32_t s = P.ctl->superstep;
     float* nxt = (s & 1) ? P.contrib1 : P.contrib0;
-    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t full0 = pb_smem(bars), empty0 = pb_smem(bars + PB_STAGES);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < PB_STAGES; ++i) {
+            pb_mbar_init(full0 + 8 * i, 1);
+            pb_mbar_init(empty0 + 8 * i, PB2_CONSUMERS);
+        }
+        pb_mbar_init(pb_smem(cbar), PB2_CONSUMERS);
+        pb_mbar_init(pb_smem(cbar + 1), PB2_CONSUMERS);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        if (blockIdx.x == 0) B.ctr[0] = 0;  // phase 1 of the next superstep claims from 0
+    }
+    for (uint32_t i = threadIdx.x; i < PB_BIN_V; i += blockDim.x) acc_lo[i] = 0;
+    __syncthreads();
+
+    if (warp == 0) {  // ------------------------------------------------ producer
+        if (lane != 0) return;
+        uint32_t k = 0;
+        bool ok = true;
+        for (bool more = true; more && ok;) {
+            const uint32_t t = atomicAdd(B.ctr + 1, 1u);
+            more = t < B.n_tasks;
+            const uint4 tk = more ? B.tasks[t] : make_uint4(0, 0, 0, 0);
+            const uint32_t n = tk.w - tk.z;
+            const uint32_t ntiles = more ? max(1u, (n + PB_TILE - 1) / PB_TILE) : 1u;
+            for (uint32_t j = 0; j < ntiles; ++j, ++k) {
+                const uint32_t st = k % PB_STAGES, r = k / PB_STAGES;
+                if (r >= 1 && !pb_mbar_wait(empty0 + 8 * st, (r - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t cnt = more ? min(PB_TILE, n - j * PB_TILE) : 0u;
+                meta[2 * st] = make_uint4(more ? tk.x : INF, tk.y, j, ntiles);  // {first vertex, vertices, tile, tiles}
+                meta[2 * st + 1] = make_uint4(cnt, 0, 0, 0);
+                if (cnt) {
+                    pb_mbar_arrive_tx(full0 + 8 * st, cnt * 6u);
+                    pb_bulk_load(pb_smem(ring_code + st * PB_TILE), B.code + tk.z + j * PB_TILE, cnt * 4u, full0 + 8 * st);
+                    pb_bulk_load(pb_smem(ring_dst + st * PB_TILE), B.dst + tk.z + j * PB_TILE, cnt * 2u, full0 + 8 * st);
+                } else {
+                    pb_mbar_arrive(full0 + 8 * st);
+                }
+            }
+        }
+        if (!ok) {  // record the timeout, then wait (bounded) for the copies still in flight
+            atomicOr(&P.ctl->err, 2u);
+            for (uint32_t q = k > PB_STAGES ? k - PB_STAGES : 0; q < k; ++q)
+                (void)pb_mbar_wait(full0 + 8 * (q % PB_STAGES), (q / PB_STAGES) & 1);
+        }
+        return;
+    }
+
+    // --------------------------------------------------------------- consumers
+    const uint32_t c = threadIdx.x - 32;  // 0 .. 32 * PB2_CONSUMERS - 1
     const float inv_scale = B.inv_scale;
-    if (blockIdx.x == 0 && threadIdx.x == 0) B.ctr[0] = 0;  // phase 1 of the next superstep claims from 0
-    for (;;) {
-        if (threadIdx.x == 0) task = atomicAdd(B.ctr + 1, 1u);
-        __syncthreads();
-        const uint32_t t = task;
-        if (t >= B.n_tasks) break;
-        const uint4 tk = B.tasks[t];  // {first vertex, vertices, first unit, end unit}
-        const uint32_t v0 = tk.x, nv = tk.y, ue = tk.w;
-        uint32_t* hi = B.hi + v0;
-        for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x) acc_lo[i] = 0;
-        if (threadIdx.x == 0) next_unit = tk.z;
-        __syncthreads();
-        auto claim = [&](uint32_t& u, uint32_t& my) {
-            uint32_t c = 0;
-            if (lane == 0) c = atomicAdd(&next_unit, 32u);
-            u = __shfl_sync(FULL, c, 0);
-            my = u + lane < ue ? __ldcs(B.units + u + lane) : 0u;
-        };
-        uint32_t u0, my0, u1, my1;
-        claim(u0, my0);
-        claim(u1, my1);
-        PbClaim x0, x1;
-        if (u0 < ue) pb_load(B, u0, my0, ue, lane, x0);
-        while (u0 < ue) {
-            uint32_t u2, my2;
-            claim(u2, my2);
-            if (u1 < ue) pb_load(B, u1, my1, ue, lane, x1);
-            pb_accumulate_claim(B, acc_lo, hi, x0, my0, lane);
-            u0 = u1;
-            my0 = my1;
-            x0 = x1;
-            u1 = u2;
-            my1 = my2;
+    const uint32_t cb0 = pb_smem(cbar), cb1 = pb_smem(cbar + 1);
+    uint32_t bins_done = 0;
+    for (uint32_t k = 0;; ++k) {
+        const uint32_t st = k % PB_STAGES, r = k / PB_STAGES;
+        if (!pb_mbar_wait(full0 + 8 * st, r & 1)) {
+            atomicOr(&P.ctl->err, 2u);
+            break;
         }
-        __syncthreads();  // also orders this CTA's high-word atomics before the reads below
-        for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x) {
-            const uint32_t h = __ldcg(hi + i);
-            if (h) hi[i] = 0;
-            pr_finish(P, v0 + i, pb_value(h, acc_lo[i], inv_scale), s, nxt);
+        const uint4 m = meta[2 * st];  // {first vertex, vertices, tile, tiles}
+        const uint32_t cnt = meta[2 * st + 1].x;
+        if (m.x == INF) break;
+        uint32_t* hi = B.hi + m.x;
+#pragma unroll
+        for (int gq = 0; gq < PB_GROUPS; ++gq) {
+            const uint32_t i = 4 * (c + gq * 32 * PB2_CONSUMERS);
+            uint32_t flags = 0;  // bit q: carry or big in entry i + q
+            uint4 cv = make_uint4(0, 0, 0, 0);
+            uint2 dv = make_uint2(0, 0);
+            if (i < cnt) {
+                cv = *reinterpret_cast<const uint4*>(ring_code + st * PB_TILE + i);
+                dv = *reinterpret_cast<const uint2*>(ring_dst + st * PB_TILE + i);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t code = q == 0 ? cv.x : q == 1 ? cv.y : q == 2 ? cv.z : cv.w;
+                    const uint32_t d = ((q < 2 ? dv.x : dv.y) >> (16 * (q & 1))) & 0xFFFFu;
+                    const uint32_t big = code >> 31;
+                    const uint32_t v = big ? 0u : code;
+                    const uint32_t old = atomicAdd(acc_lo + d, v);
+                    flags |= ((old + v < old ? 1u : 0u) | big) << q;
+                }
+            }
+            if (__any_sync(FULL, flags)) {
+                for (int q = 0; q < 4; ++q)
+                    if ((flags >> q) & 1u) {
+                        const uint32_t code = q == 0 ? cv.x : q == 1 ? cv.y : q == 2 ? cv.z : cv.w;
+                        const uint32_t d = ((q < 2 ? dv.x : dv.y) >> (16 * (q & 1))) & 0xFFFFu;
+                        if (code >> 31)
+                            pb_add_big(B, acc_lo, hi, d, code);
+                        else  // the carry of the common path (a big entry added 0 there and cannot carry)
+                            atomicAdd(hi + d, 1u);
+                    }
+            }
         }
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) pb_mbar_arrive(empty0 + 8 * st);
+        if (m.z + 1 == m.w) {  // the bin's last tile: every code is in
+            // the barrier also orders the high-word atomics before the reads below
+            bool ok = pb_consumer_sync(cb0, bins_done & 1, lane);
+            pb_finish(P, hi, acc_lo, m.x, m.y, c, 32 * PB2_CONSUMERS, s, nxt, inv_scale);
+            ok = pb_consumer_sync(cb1, bins_done & 1, lane) && ok;
+            ++bins_done;
+            if (!ok) {
+                if (lane == 0) atomicOr(&P.ctl->err, 2u);
+                break;
+            }
+        }
     }
 }
 
@@ -268,75 +430,110 @@ __device__ __forceinline__ void pb_hist(const uint32_t* __restrict__ col, const 
     __syncthreads();
 }
 
-__device__ __forceinline__ uint32_t pad8(uint32_t n) { return (n + 7) & ~7u; }
+__device__ __forceinline__ uint32_t pad4(uint32_t n) { return (n + 3) & ~3u; }
 
-// Per chunk: units (8 entries, runs padded to whole units) per bin, and the
-// chunk's unit count.
+// Per chunk: its row of the chunk x bin matrix of run lengths padded to 4
+// entries, its number of runs and its padded entry count.
 __global__ void __launch_bounds__(PBB_THREADS) k_pb_count(const uint32_t* __restrict__ csr_off,
                                                           const uint32_t* __restrict__ col,
-                                                          const uint2* __restrict__ cs,
+                                                          const uint4* __restrict__ cs,
                                                           const uint32_t* __restrict__ binof, uint32_t nb,
-                                                          uint32_t* unit_count, uint32_t* chunk_units) {
+                                                          uint32_t* M, uint32_t* chunk_runs, uint32_t* chunk_len) {
     extern __shared__ uint32_t hist[];
     const uint32_t c = blockIdx.x;
     pb_hist(col, binof, csr_off[cs[c].x], csr_off[cs[c].x + cs[c].y], nb, hist);
-    uint32_t mine = 0;
+    uint32_t runs = 0, len = 0;
     for (uint32_t q = threadIdx.x; q < nb; q += blockDim.x) {
-        const uint32_t n = pad8(hist[q]) >> 3;
-        if (n) atomicAdd(unit_count + q, n);
-        mine += n;
+        const uint32_t n4 = pad4(hist[q]);
+        M[(size_t)c * nb + q] = n4;
+        runs += n4 ? 1u : 0u;
+        len += n4;
     }
-    for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(FULL, mine, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(chunk_units + c, mine);
+    for (int o = 16; o; o >>= 1) {
+        runs += __shfl_xor_sync(FULL, runs, o);
+        len += __shfl_xor_sync(FULL, len, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(chunk_runs + c, runs);
+        atomicAdd(chunk_len + c, len);
+    }
 }
 
-// Per chunk: place every out-edge into its bin's run, pad the run to whole units
-// with entries of source `ns` (whose staged code is 0), and list the units.
+// Per bin: exclusive scan of its column over the chunks (the place of every
+// padded run inside its bin), and the bin's padded total.
+__global__ void k_pb_colscan(uint32_t* M, uint32_t nC, uint32_t nb, uint32_t* total) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb) return;
+    uint32_t run = 0;
+    for (uint32_t c = 0; c < nC; ++c) {
+        const uint32_t t = M[(size_t)c * nb + q];
+        M[(size_t)c * nb + q] = run;
+        run += t;
+    }
+    total[q] = run;
+}
+
+// Per chunk: the run records (padded to 4 entries, the padding reads source
+// `ns` whose code is 0), then every out-edge into its run in both orders.
 __global__ void __launch_bounds__(PBB_THREADS) k_pb_place(const uint32_t* __restrict__ csr_off,
                                                           const uint32_t* __restrict__ col,
-                                                          const uint2* __restrict__ cs,
-                                                          const uint32_t* __restrict__ pbase,
+                                                          const uint4* __restrict__ cs,
+                                                          const uint32_t* __restrict__ abase,
                                                           const uint32_t* __restrict__ binof,
-                                                          const uint32_t* __restrict__ bstart, uint32_t nb,
-                                                          const uint32_t* __restrict__ unit_off, uint32_t* unit_cur,
-                                                          uint32_t* units, uint16_t* src, uint16_t* dst) {
+                                                          const uint32_t* __restrict__ bstart,
+                                                          const uint32_t* __restrict__ bbase, uint32_t nb,
+                                                          const uint32_t* __restrict__ M, uint4* runs,
+                                                          uint16_t* src, uint16_t* dst) {
     extern __shared__ uint32_t sm[];
-    uint32_t* cnt = sm;        // [nb]: entries per bin, then the placement cursor
-    uint32_t* offs = sm + nb;  // [ns + 1]: the chunk's CSR offsets
-    __shared__ uint32_t wsum[PBB_THREADS / 32];
-    const uint32_t c = blockIdx.x, s0 = cs[c].x, ns = cs[c].y, p0 = pbase[c];
+    uint32_t* cnt = sm;             // [nb]: entries per bin, then the run's offset inside the chunk
+    uint32_t* cur = sm + nb;        // [nb]: placement cursor
+    uint32_t* offs = sm + 2 * nb;   // [ns + 1]: the chunk's CSR offsets
+    __shared__ uint32_t wsum[PBB_THREADS / 32], wnz[PBB_THREADS / 32];
+    const uint4 ch = cs[blockIdx.x];
+    const uint32_t s0 = ch.x, ns = ch.y, a_c = abase[blockIdx.x];
+    const uint32_t* Mc = M + (size_t)blockIdx.x * nb;
     for (uint32_t i = threadIdx.x; i <= ns; i += blockDim.x) offs[i] = csr_off[s0 + i];
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = 0;
     pb_hist(col, binof, csr_off[s0], csr_off[s0 + ns], nb, cnt);
     const uint32_t e0 = offs[0], e1 = offs[ns];
-    // exclusive scan of the padded counts: thread t owns bins [b0, b1)
+    // exclusive scans of the padded counts and of the non-empty bins: thread t owns bins [b0, b1)
     const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
     const uint32_t b0 = min(nb, threadIdx.x * per), b1 = min(nb, b0 + per);
-    uint32_t mine = 0;
-    for (uint32_t q = b0; q < b1; ++q) mine += pad8(cnt[q]);
-    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t inc = mine;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, inc, o);
-        if (lane >= (uint32_t)o) inc += y;
-    }
-    if (lane == 31) wsum[w] = inc;
-    __syncthreads();
-    uint32_t run = inc - mine;
-    for (uint32_t k = 0; k < w; ++k) run += wsum[k];
+    uint32_t mine = 0, mnz = 0;
     for (uint32_t q = b0; q < b1; ++q) {
-        const uint32_t n = cnt[q], n8 = pad8(n);
+        mine += pad4(cnt[q]);
+        mnz += cnt[q] ? 1u : 0u;
+    }
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = mine, inz = mnz;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, inc, o), z = __shfl_up_sync(FULL, inz, o);
+        if (lane >= (uint32_t)o) {
+            inc += y;
+            inz += z;
+        }
+    }
+    if (lane == 31) {
+        wsum[w] = inc;
+        wnz[w] = inz;
+    }
+    __syncthreads();
+    uint32_t off = inc - mine, rk = inz - mnz;
+    for (uint32_t k = 0; k < w; ++k) {
+        off += wsum[k];
+        rk += wnz[k];
+    }
+    for (uint32_t q = b0; q < b1; ++q) {
+        const uint32_t n = cnt[q], n4 = pad4(n);
         if (n) {
-            const uint32_t nu = n8 >> 3;
-            const uint32_t slot = unit_off[q] + atomicAdd(unit_cur + q, nu);
-            const uint32_t first = (p0 + run) >> 3;
-            for (uint32_t k = 0; k < nu; ++k) units[slot + k] = first + k;
-            for (uint32_t k = n; k < n8; ++k) {
-                src[p0 + run + k] = (uint16_t)ns;
-                dst[p0 + run + k] = 0;
+            runs[ch.z + rk++] = make_uint4(a_c + off, bbase[q] + Mc[q], n4, 0u);
+            for (uint32_t k = n; k < n4; ++k) {
+                src[a_c + off + k] = (uint16_t)ns;
+                dst[bbase[q] + Mc[q] + k] = 0;
             }
         }
-        cnt[q] = run;
-        run += n8;
+        cnt[q] = off;
+        off += n4;
     }
     __syncthreads();
     for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -349,9 +546,9 @@ __global__ void __launch_bounds__(PBB_THREADS) k_pb_place(const uint32_t* __rest
             else
                 hi = mid;
         }
-        const uint32_t pos = p0 + atomicAdd(cnt + q, 1u);
-        src[pos] = (uint16_t)lo;
-        dst[pos] = (uint16_t)(v - bstart[q]);
+        const uint32_t k = atomicAdd(cur + q, 1u);
+        src[a_c + cnt[q] + k] = (uint16_t)lo;
+        dst[bbase[q] + Mc[q] + k] = (uint16_t)(v - bstart[q]);
     }
 }
 
@@ -425,7 +622,7 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB1_SMEM)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB2_SMEM)));
     L->grid1 = occupancy_grid(g, (const void*)k_pb_scatter, PB1_THREADS, PB1_SMEM);
-    L->grid2 = occupancy_grid(g, (const void*)k_pb_accumulate, PB2_THREADS, PB2_SMEM);
+    L->grid2 = g->num_sms;  // one producer/consumer CTA per SM
 
     // chunks of consecutive sources, cut by edge count and by source count; runs of
     // sources without out-edges that would form a chunk of their own are skipped
@@ -456,93 +653,105 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     off.clear();
     off.shrink_to_fit();
 
-    uint2* d_cs;
-    uint32_t *d_pbase, *d_unit_count, *d_corder, *d_chunk_units;
+    uint4* d_cs;
+    uint32_t* d_bstart;
     PBK(pb_alloc(g, L, &d_cs, nC));
-    PBK(pb_alloc(g, L, &d_pbase, nC + 1));
-    PBK(pb_alloc(g, L, &d_corder, nC));
-    PBK(pb_alloc(g, L, &d_chunk_units, nC));
-    PBK(pb_alloc(g, L, &d_unit_count, nb));
-    TmpBuf t_binof{g}, t_bstart{g}, t_unit_cur{g}, t_unit_off{g};
-    uint32_t *d_binof, *d_bstart, *d_unit_cur, *d_unit_off;
+    TmpBuf t_binof{g}, t_bstart{g}, t_M{g}, t_chunk_runs{g}, t_chunk_len{g}, t_total{g}, t_bbase{g}, t_abase{g};
+    uint32_t *d_binof, *d_M, *d_chunk_runs, *d_chunk_len, *d_total, *d_bbase, *d_abase;
     PBK(t_binof.alloc(&d_binof, V));
     PBK(t_bstart.alloc(&d_bstart, nb + 1));
-    PBK(t_unit_cur.alloc(&d_unit_cur, nb));
-    PBK(t_unit_off.alloc(&d_unit_off, nb + 1));
-    if (nC) PBK(cuda_err(cudaMemcpyAsync(d_cs, chunks.data(), sizeof(uint2) * nC, cudaMemcpyHostToDevice, st)));
+    PBK(t_M.alloc(&d_M, (size_t)nC * nb));
+    PBK(t_chunk_runs.alloc(&d_chunk_runs, nC));
+    PBK(t_chunk_len.alloc(&d_chunk_len, nC));
+    PBK(t_abase.alloc(&d_abase, nC));
+    PBK(t_total.alloc(&d_total, nb));
+    PBK(t_bbase.alloc(&d_bbase, nb + 1));
+    std::vector<uint4> cinfo(nC);
+    for (uint32_t c = 0; c < nC; ++c) cinfo[c] = make_uint4(chunks[c].x, chunks[c].y, 0, 0);
+    if (nC) PBK(cuda_err(cudaMemcpyAsync(d_cs, cinfo.data(), sizeof(uint4) * nC, cudaMemcpyHostToDevice, st)));
     PBK(cuda_err(cudaMemcpyAsync(d_bstart, bstart.data(), sizeof(uint32_t) * (nb + 1), cudaMemcpyHostToDevice, st)));
-    PBK(cuda_err(cudaMemsetAsync(d_unit_count, 0, sizeof(uint32_t) * nb, st)));
-    PBK(cuda_err(cudaMemsetAsync(d_unit_cur, 0, sizeof(uint32_t) * nb, st)));
-    PBK(cuda_err(cudaMemsetAsync(d_chunk_units, 0, sizeof(uint32_t) * std::max<uint32_t>(nC, 1), st)));
+    PBK(cuda_err(cudaMemsetAsync(d_chunk_runs, 0, sizeof(uint32_t) * std::max<uint32_t>(nC, 1), st)));
+    PBK(cuda_err(cudaMemsetAsync(d_chunk_len, 0, sizeof(uint32_t) * std::max<uint32_t>(nC, 1), st)));
     k_pb_binof<<<nb, 256, 0, st>>>(d_bstart, d_binof);
     const size_t smem_count = sizeof(uint32_t) * nb;
-    const size_t smem_place = sizeof(uint32_t) * (nb + PB_MAXS + 1);
+    const size_t smem_place = sizeof(uint32_t) * (2 * nb + PB_MAXS + 1);
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_count)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place)));
-    if (nC)
-        k_pb_count<<<nC, PBB_THREADS, smem_count, st>>>(g->csr_off, g->csr_col, d_cs, d_binof, nb, d_unit_count,
-                                                        d_chunk_units);
-    PBK(cuda_err(cudaGetLastError()));
-    std::vector<uint32_t> unit_off(nb + 1, 0), chunk_units(nC);
-    PBK(cuda_err(cudaMemcpyAsync(unit_off.data() + 1, d_unit_count, sizeof(uint32_t) * nb, cudaMemcpyDeviceToHost, st)));
-    if (nC)
-        PBK(cuda_err(cudaMemcpyAsync(chunk_units.data(), d_chunk_units, sizeof(uint32_t) * nC, cudaMemcpyDeviceToHost, st)));
-    PBK(cuda_err(cudaStreamSynchronize(st)));
-    uint64_t total_units = 0;
-    for (uint32_t q = 0; q < nb; ++q) {
-        total_units += unit_off[q + 1];
-        if (total_units >= (1ull << 29)) PBK(IP_E_RANGE);  // entries must be indexable by uint32
-        unit_off[q + 1] = (uint32_t)total_units;
+    if (nC) {
+        k_pb_count<<<nC, PBB_THREADS, smem_count, st>>>(g->csr_off, g->csr_col, d_cs, d_binof, nb, d_M,
+                                                        d_chunk_runs, d_chunk_len);
+        k_pb_colscan<<<(nb + 255) / 256, 256, 0, st>>>(d_M, nC, nb, d_total);
+    } else {
+        PBK(cuda_err(cudaMemsetAsync(d_total, 0, sizeof(uint32_t) * nb, st)));
     }
-    std::vector<uint32_t> pbase(nC + 1, 0);
-    for (uint32_t c = 0; c < nC; ++c) pbase[c + 1] = pbase[c] + 8 * chunk_units[c];
-    const uint64_t P_total = (uint64_t)pbase[nC];
-    PBK(cuda_err(cudaMemcpyAsync(d_unit_off, unit_off.data(), sizeof(uint32_t) * (nb + 1), cudaMemcpyHostToDevice, st)));
-    PBK(cuda_err(cudaMemcpyAsync(d_pbase, pbase.data(), sizeof(uint32_t) * (nC + 1), cudaMemcpyHostToDevice, st)));
-    uint32_t *d_units, *d_code, *d_hi;
+    PBK(cuda_err(cudaGetLastError()));
+    std::vector<uint32_t> total(nb), chunk_runs(nC), chunk_len(nC), abase(nC);
+    PBK(cuda_err(cudaMemcpyAsync(total.data(), d_total, sizeof(uint32_t) * nb, cudaMemcpyDeviceToHost, st)));
+    if (nC) {
+        PBK(cuda_err(cudaMemcpyAsync(chunk_runs.data(), d_chunk_runs, sizeof(uint32_t) * nC, cudaMemcpyDeviceToHost, st)));
+        PBK(cuda_err(cudaMemcpyAsync(chunk_len.data(), d_chunk_len, sizeof(uint32_t) * nC, cudaMemcpyDeviceToHost, st)));
+    }
+    PBK(cuda_err(cudaStreamSynchronize(st)));
+    // bin-major places of the bins (padded to 8 entries) and run records per chunk
+    std::vector<uint32_t> bbase(nb + 1, 0);
+    uint64_t acc = 0;
+    for (uint32_t q = 0; q < nb; ++q) {
+        bbase[q] = (uint32_t)acc;
+        acc += (total[q] + 7ull) & ~7ull;
+        if (acc >= 0xFFFFFFF0ull) PBK(IP_E_RANGE);  // entries must be indexable by uint32
+    }
+    bbase[nb] = (uint32_t)acc;
+    const uint64_t P_total = acc;
+    uint64_t R = 0, A = 0;
+    for (uint32_t c = 0; c < nC; ++c) {
+        cinfo[c].z = (uint32_t)R;
+        R += chunk_runs[c];
+        cinfo[c].w = (uint32_t)R;
+        abase[c] = (uint32_t)A;
+        A += chunk_len[c];
+    }
+    if (A >= 0xFFFFFFF0ull) PBK(IP_E_RANGE);
+    if (nC) PBK(cuda_err(cudaMemcpyAsync(d_abase, abase.data(), sizeof(uint32_t) * nC, cudaMemcpyHostToDevice, st)));
+    if (nC) PBK(cuda_err(cudaMemcpyAsync(d_cs, cinfo.data(), sizeof(uint4) * nC, cudaMemcpyHostToDevice, st)));
+    PBK(cuda_err(cudaMemcpyAsync(d_bbase, bbase.data(), sizeof(uint32_t) * (nb + 1), cudaMemcpyHostToDevice, st)));
+    uint4* d_runs;
+    uint32_t *d_code, *d_hi;
     uint16_t *d_src, *d_dst;
     unsigned long long* d_big;
-    PBK(pb_alloc(g, L, &d_units, total_units));
-    PBK(pb_alloc(g, L, &d_src, P_total));
+    PBK(pb_alloc(g, L, &d_runs, R));
+    PBK(pb_alloc(g, L, &d_src, A));
     PBK(pb_alloc(g, L, &d_dst, P_total));
     PBK(pb_alloc(g, L, &d_code, P_total));
     PBK(pb_alloc(g, L, &d_big, V));
     PBK(pb_alloc(g, L, &d_hi, V));
     PBK(cuda_err(cudaMemsetAsync(d_hi, 0, sizeof(uint32_t) * V, st)));
+    // padding entries keep code 0 and destination 0: phase 1 never writes them
+    PBK(cuda_err(cudaMemsetAsync(d_dst, 0, sizeof(uint16_t) * std::max<uint64_t>(P_total, 1), st)));
+    PBK(cuda_err(cudaMemsetAsync(d_code, 0, sizeof(uint32_t) * std::max<uint64_t>(P_total, 1), st)));
     if (nC)
-        k_pb_place<<<nC, PBB_THREADS, smem_place, st>>>(g->csr_off, g->csr_col, d_cs, d_pbase, d_binof, d_bstart, nb,
-                                                        d_unit_off, d_unit_cur, d_units, d_src, d_dst);
+        k_pb_place<<<nC, PBB_THREADS, smem_place, st>>>(g->csr_off, g->csr_col, d_cs, d_abase, d_binof, d_bstart,
+                                                        d_bbase, nb, d_M, d_runs, d_src, d_dst);
     PBK(cuda_err(cudaGetLastError()));
 
-    // phase-2 tasks, one per bin, in bin order: neighbouring bins run at the same
-    // time, so the sectors their runs share at chunk-region boundaries are read
-    // from DRAM once. Phase-1 chunks, largest first.
+    // phase-2 tasks, one per bin, in bin order
     std::vector<uint4> tasks(nb);
-    for (uint32_t q = 0; q < nb; ++q)
-        tasks[q] = make_uint4(bstart[q], bstart[q + 1] - bstart[q], unit_off[q], unit_off[q + 1]);
-    std::vector<uint32_t> corder(nC);
-    std::iota(corder.begin(), corder.end(), 0u);
-    std::stable_sort(corder.begin(), corder.end(),
-                     [&](uint32_t a, uint32_t b) { return chunk_units[a] > chunk_units[b]; });
+    for (uint32_t q = 0; q < nb; ++q) tasks[q] = make_uint4(bstart[q], bstart[q + 1] - bstart[q], bbase[q], bbase[q + 1]);
     uint4* d_tasks;
     uint32_t* d_ctr;
     PBK(pb_alloc(g, L, &d_tasks, nb));
     PBK(pb_alloc(g, L, &d_ctr, 2));
     PBK(cuda_err(cudaMemcpyAsync(d_tasks, tasks.data(), sizeof(uint4) * nb, cudaMemcpyHostToDevice, st)));
-    if (nC) PBK(cuda_err(cudaMemcpyAsync(d_corder, corder.data(), sizeof(uint32_t) * nC, cudaMemcpyHostToDevice, st)));
     PBK(cuda_err(cudaMemsetAsync(d_ctr, 0, sizeof(uint32_t) * 2, st)));
     PBK(cuda_err(cudaStreamSynchronize(st)));
 
     d.n_chunks = nC;
     d.n_tasks = nb;
     d.chunk = d_cs;
-    d.pbase = d_pbase;
-    d.corder = d_corder;
+    d.runs = d_runs;
     d.src = d_src;
     d.dst = d_dst;
     d.code = d_code;
     d.big = d_big;
-    d.units = d_units;
     d.tasks = d_tasks;
     d.hi = d_hi;
     d.ctr = d_ctr;
@@ -575,7 +784,7 @@ int pb_prepare(ip_graph* g, cudaStream_t st, PbDev* out) {
 int pb_launch(const ip_graph* g, const Params& P, cudaStream_t st) {
     const PbLayout* L = static_cast<const PbLayout*>(g->pb);
     k_pb_scatter<<<L->grid1, PB1_THREADS, PB1_SMEM, st>>>(P);
-    k_pb_accumulate<<<L->grid2, PB2_THREADS, PB2_SMEM, st>>>(P);
+    k_pb_accumulate<<<L->grid2, 32 * (PB2_CONSUMERS + 1), PB2_SMEM, st>>>(P);
     return cuda_err(cudaGetLastError());
 }
 

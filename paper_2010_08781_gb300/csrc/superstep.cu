@@ -1294,6 +1294,7 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     const DevCtl& c = *g->ctl_host;
     const uint32_t supersteps = c.superstep + 1;
     g->last_app = app;
+    if (c.err & 2u) return IP_E_TIMEOUT;  // a bounded wait of a kernel ran out
     if (c.err) return IP_E_DEVICE_ASSERT;
     if (stats) {
         stats->supersteps = supersteps;
