@@ -299,6 +299,16 @@ def oracle_step(g):
     return int(a["messages"].sum()) + int(b["messages"].sum()), dt
 
 
+def cpu_oracle_pagerank(g, T, sample):
+    """The FP64 oracle's PageRank on the host cores (single-threaded), GTEPS = T*E / s."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.pagerank(g.n, g.row_ptr, g.col, T=T)
+    dt = time.perf_counter() - t0
+    return {"value": round(T * g.m / dt / 1e9, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample,
+            "seconds": round(dt, 2)}
+
+
 def cpu_baseline(g):
     m, dt = oracle_step(g)
     return {"value": round(m / dt / 1e9, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
@@ -358,18 +368,25 @@ def ncu_case(spec, scale):
                       "ms": round(st.elapsed_ms, 4)}))
 
 
-def pr_measure(G, V, E, reps=3, T=30):
-    """PageRank pull, T iterations: device time of the run and the k_pr_pull roofline
-    (8E + 16V + 4(V+1) algorithmic bytes per launch, CUDA events per launch)."""
+def pr_measure(G, V, E, reps=3, T=30, engine="auto"):
+    """PageRank pull, T iterations: device time of the run and the roofline of its
+    pull exchange (the CSC gather k_pr_pull, or the blocked pull's two launches
+    k_pb_scatter + k_pb_accumulate): algorithmic bytes 8E + 16V + 4(V+1) per
+    superstep (in-edge indices and their sources' broadcasts; offsets, ranks,
+    broadcasts, out-degrees) over the exchange time, CUDA events per superstep."""
     peak, kind = measured_peaks()
-    ts = [G.run("pagerank", policy="forced", forced_mode="pull", pr_iterations=T).elapsed_ms for _ in range(reps)]
-    st = G.run("pagerank", policy="forced", forced_mode="pull", pr_iterations=T, profile_kernels=1)
+    kw = dict(policy="forced", forced_mode="pull", pr_iterations=T, pr_engine=engine)
+    ts = [G.run("pagerank", **kw).elapsed_ms for _ in range(reps)]
+    st = G.run("pagerank", profile_kernels=1, **kw)
     kms = [float(x) for x in st.kernel_ms[1:st.supersteps, 1]]
     by = 4 * (V + 1) + 8 * E + 16 * V
     avg = sum(kms) / len(kms)
     ach = by / (avg * 1e-3) / 1e9
-    return {"gteps": round(T * E / (min(ts) * 1e-3) / 1e9, 2), "ms": round(min(ts), 4),
-            "roofline": {"bound": "hbm", "kernel": "k_pr_pull", "achieved": round(ach, 1), "peak": peak,
+    blocked = engine == "blocked" or (engine == "auto" and E >= 1 << 24)
+    kern = "k_pb_scatter+k_pb_accumulate" if blocked else "k_pr_pull"
+    return {"engine": "blocked" if blocked else "gather", "gteps": round(T * E / (min(ts) * 1e-3) / 1e9, 2),
+            "ms": round(min(ts), 4), "ms_per_iteration": round(min(ts) / T, 4),
+            "roofline": {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": peak,
                          "peak_kind": kind, "unit": "GB/s", "frac": round(ach / peak, 4),
                          "avg_launch_us": round(1e3 * avg, 2), "bytes_per_launch": by}}
 
@@ -385,6 +402,7 @@ def run_config(args):
         g = inputs.rmat_graph(16, seed=1)
         with ipg.Graph.from_inputs(g) as G:
             out["pagerank"] = pr_measure(G, g.n, g.m)
+        out["cpu_oracle"] = cpu_oracle_pagerank(g, 30, "PageRank T=30 on the full graph")
         out["workload"] = "PageRank T=30 on directed R-MAT scale 16 (edge factor 16, seed 1)"
         out["edges"] = g.m
     elif args.config == "c4":  # batched
@@ -418,10 +436,12 @@ def run_config(args):
     elif args.config == "c5":  # billion-edge
         g = inputs.rmat_graph(26, seed=1)
         V, E = g.n, g.m
+        out["cpu_oracle_pagerank"] = cpu_oracle_pagerank(g, 1, "PageRank with T=1 (one rank update) on the full graph")
         with ipg.Graph(V, g.row_ptr, g.col) as G:  # in-edges transposed on the device
             del g
             out["pagerank"] = pr_measure(G, V, E, reps=2)
             out["pagerank"]["vertices"], out["pagerank"]["edges"] = V, E
+            out["pagerank_gather"] = pr_measure(G, V, E, reps=2, engine="gather")
         src, dst = inputs.rmat_edges(26, 16 << 26, seed=1)
         gs = inputs.from_edges(1 << 26, src, dst, symmetrize=True)
         del src, dst
