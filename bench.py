@@ -43,6 +43,19 @@ def build_graph(scale=SCALE):
                              weighted=True, wseed=1)
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum) of a
+    kernel on the workload it is reported for, from profiles/traffic.json (written
+    from an ncu capture of the same command; None when not captured)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    return None if e is None else e.get("bytes_per_launch")
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -233,7 +246,7 @@ def run_gpu(args, rank, world, local_rank):
     achieved = d_bytes / (d_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "launches_per_step": d_n / args.steps,
+                "traffic": measured_traffic(dom), "launches_per_step": d_n / args.steps,
                 "avg_launch_us": round(1e3 * d_ms / d_n, 2)}
     total_k = sum(v[0] for v in kern.values())
     roofline["share_of_kernel_time"] = round(d_ms / total_k, 3)
@@ -388,6 +401,7 @@ def pr_measure(G, V, E, reps=3, T=30, engine="auto"):
             "ms": round(min(ts), 4), "ms_per_iteration": round(min(ts) / T, 4),
             "roofline": {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": peak,
                          "peak_kind": kind, "unit": "GB/s", "frac": round(ach / peak, 4),
+                         "traffic": measured_traffic(kern) if E >= 1 << 30 else None,
                          "avg_launch_us": round(1e3 * avg, 2), "bytes_per_launch": by}}
 
 

@@ -46,16 +46,16 @@ namespace ipg {
 namespace {
 
 constexpr uint32_t PB_MAXS = 16384;      // sources per chunk: their codes fit 64 KB of shared memory
-constexpr uint32_t PB_CHUNK_E = 131072;  // target out-edges per chunk
+constexpr uint32_t PB_CHUNK_E = 262144;  // target out-edges per chunk
 constexpr uint32_t PB_MAX_BINS = 16384;  // bins a chunk histograms in shared memory
 constexpr uint32_t PB_MAX_V = 13824u * PB_BIN_V;  // vertex-capped bins plus entry-capped ones fit PB_MAX_BINS
 constexpr int PB1_THREADS = 512, PBB_THREADS = 512;
 constexpr int PB1_LOADS = 4;         // phase 1: groups of 4 entries per lane in flight
 constexpr int PB_BATCH = 8;          // per-vertex loops (staging, compute()): loads in flight per thread
-constexpr int PB2_CONSUMERS = 16;    // phase 2: consumer warps (plus one producer warp)
+constexpr int PB2_CONSUMERS = 24;    // phase 2: consumer warps (plus one producer warp)
 constexpr int PB_GROUPS = 2;        // phase 2: groups of 4 entries per consumer thread and stage
-constexpr uint32_t PB_TILE = 4 * PB_GROUPS * 32 * PB2_CONSUMERS;  // entries per stage (4096)
-constexpr int PB_STAGES = 5;         // phase 2: stages of the bulk-copy ring (120 KB)
+constexpr uint32_t PB_TILE = 4 * PB_GROUPS * 32 * PB2_CONSUMERS;  // entries per stage (6144)
+constexpr int PB_STAGES = 3;         // phase 2: stages of the bulk-copy ring (108 KB)
 constexpr size_t PB1_SMEM = (PB_MAXS + 1) * sizeof(uint32_t);
 constexpr size_t PB2_SMEM = PB_BIN_V * sizeof(uint32_t) + (size_t)PB_STAGES * PB_TILE * (4 + 2) +
                             PB_STAGES * (32 + 16);
@@ -241,18 +241,23 @@ __device__ __forceinline__ bool pb_mbar_wait(uint32_t bar, uint32_t parity) {
 }
 
 // compute() of the bin's vertices first, first + stride, ... < nv (vertex v0 + v):
-// the sum is hi:lo in 2^-S units. PB_BATCH vertices' loads are in flight at once.
-// Clears the vertex's high word and low word for the next bin.
-__device__ __forceinline__ void pb_finish(const Params& P, uint32_t* hi, uint32_t* lo, uint32_t v0, uint32_t nv,
-                                          uint32_t first, uint32_t stride, uint32_t s, float* nxt,
-                                          float inv_scale) {
+// the sum is hi:lo in 2^-S units, the high word read only where touched marks
+// one (carries and big contributions set it). PB_BATCH vertices' loads are in
+// flight at once. Clears the vertex's high word and low word for the next bin.
+// The rank is stored only in a superstep that can be the run's last (s >= T or
+// the superstep cap): until then only the broadcast is read by anyone.
+__device__ __forceinline__ void pb_finish(const Params& P, uint32_t* hi, uint32_t* lo, const uint32_t* touched,
+                                          uint32_t v0, uint32_t nv, uint32_t first, uint32_t stride, uint32_t s,
+                                          float* nxt, float inv_scale) {
+    const bool last = s >= P.T || s + 1 >= P.max_supersteps;
     for (uint32_t b = first; b < nv; b += PB_BATCH * stride) {
         uint32_t h[PB_BATCH];
         float iod[PB_BATCH];
 #pragma unroll
         for (int u = 0; u < PB_BATCH; ++u) {
             const uint32_t v = b + u * stride;
-            h[u] = v < nv ? __ldcg(hi + v) : 0u;
+            const bool t = v < nv && ((touched[v >> 5] >> (v & 31)) & 1u);
+            h[u] = t ? __ldcg(hi + v) : 0u;
             iod[u] = v < nv ? __ldg(P.inv_outdeg + v0 + v) : 0.0f;
         }
 #pragma unroll
@@ -261,7 +266,7 @@ __device__ __forceinline__ void pb_finish(const Params& P, uint32_t* hi, uint32_
             if (v < nv) {
                 if (h[u]) hi[v] = 0;
                 const float r = fmaf(P.damping, pb_value(h[u], lo[v], inv_scale), P.pr_base);  // as pr_finish
-                P.rank[v0 + v] = r;
+                if (last) P.rank[v0 + v] = r;
                 nxt[v0 + v] = s < P.T ? r * iod[u] : 0.0f;
                 lo[v] = 0;
             }
@@ -299,6 +304,9 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
     uint4* meta = reinterpret_cast<uint4*>(ring_dst + PB_STAGES * PB_TILE);     // [PB_STAGES][2]
     uint64_t* bars = reinterpret_cast<uint64_t*>(meta + 2 * PB_STAGES);         // full[PB_STAGES], empty[PB_STAGES]
     __shared__ __align__(8) uint64_t cbar[2];                                  // consumer barriers
+    // vertices of a bin whose high word was written, by bin parity: the bitmap of
+    // bin k is cleared after its compute() while bin k+1 marks the other one
+    __shared__ uint32_t touched2[2][PB_BIN_V / 32];
     const PbDev& B = P.pb;
     const uint32_t s = P.ctl->superstep;
     float* nxt = (s & 1) ? P.contrib1 : P.contrib0;
@@ -315,6 +323,7 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
         if (blockIdx.x == 0) B.ctr[0] = 0;  // phase 1 of the next superstep claims from 0
     }
     for (uint32_t i = threadIdx.x; i < PB_BIN_V; i += blockDim.x) acc_lo[i] = 0;
+    for (uint32_t i = threadIdx.x; i < 2 * (PB_BIN_V / 32); i += blockDim.x) touched2[i / (PB_BIN_V / 32)][i % (PB_BIN_V / 32)] = 0;
     __syncthreads();
 
     if (warp == 0) {  // ------------------------------------------------ producer
@@ -392,6 +401,7 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
                     if ((flags >> q) & 1u) {
                         const uint32_t code = q == 0 ? cv.x : q == 1 ? cv.y : q == 2 ? cv.z : cv.w;
                         const uint32_t d = ((q < 2 ? dv.x : dv.y) >> (16 * (q & 1))) & 0xFFFFu;
+                        atomicOr(touched2[bins_done & 1] + (d >> 5), 1u << (d & 31));
                         if (code >> 31)
                             pb_add_big(B, acc_lo, hi, d, code);
                         else  // the carry of the common path (a big entry added 0 there and cannot carry)
@@ -404,8 +414,11 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
         if (m.z + 1 == m.w) {  // the bin's last tile: every code is in
             // the barrier also orders the high-word atomics before the reads below
             bool ok = pb_consumer_sync(cb0, bins_done & 1, lane);
-            pb_finish(P, hi, acc_lo, m.x, m.y, c, 32 * PB2_CONSUMERS, s, nxt, inv_scale);
+            uint32_t* touched = touched2[bins_done & 1];
+            pb_finish(P, hi, acc_lo, touched, m.x, m.y, c, 32 * PB2_CONSUMERS, s, nxt, inv_scale);
             ok = pb_consumer_sync(cb1, bins_done & 1, lane) && ok;
+            // bin k+1 marks the other bitmap; this one is clear before bin k+2 starts
+            for (uint32_t i = c; i < PB_BIN_V / 32; i += 32 * PB2_CONSUMERS) touched[i] = 0;
             ++bins_done;
             if (!ok) {
                 if (lane == 0) atomicOr(&P.ctl->err, 2u);
