@@ -9,7 +9,8 @@
 // propagation-blocking idea (Beamer, Asanovic and Patterson, IPDPS 2017):
 //
 //   layout (built once per graph): the out-edges are cut into chunks of
-//   consecutive sources (at most PB_MAXS sources, about PB_CHUNK_E edges), the
+//   consecutive sources (at most PB_MAXS sources, about E / 4096 out-edges,
+//   clamped to [PB_CHUNK_MIN, PB_CHUNK_MAX]: longer chunks give longer runs), the
 //   vertices into bins of consecutive destinations (at most PB_BIN_V vertices and
 //   about E / (4 x phase-2 CTAs) in-edges, so that every bin is a balanced task).
 //   A run is the edges of one chunk into one bin, padded to a multiple of 4
@@ -46,7 +47,7 @@ namespace ipg {
 namespace {
 
 constexpr uint32_t PB_MAXS = 16384;      // sources per chunk: their codes fit 64 KB of shared memory
-constexpr uint32_t PB_CHUNK_E = 262144;  // target out-edges per chunk
+constexpr uint32_t PB_CHUNK_MIN = 65536, PB_CHUNK_MAX = 262144;  // target out-edges per chunk
 constexpr uint32_t PB_MAX_BINS = 16384;  // bins a chunk histograms in shared memory
 constexpr uint32_t PB_MAX_V = 13824u * PB_BIN_V;  // vertex-capped bins plus entry-capped ones fit PB_MAX_BINS
 constexpr int PB1_THREADS = 512, PBB_THREADS = 512;
@@ -643,10 +644,11 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     PBK(cuda_err(cudaMemcpyAsync(off.data(), g->csr_off, sizeof(uint32_t) * (V + 1), cudaMemcpyDeviceToHost, st)));
     PBK(cuda_err(cudaStreamSynchronize(st)));
     std::vector<uint2> chunks;
+    const uint64_t chunk_e = std::min<uint64_t>(PB_CHUNK_MAX, std::max<uint64_t>(PB_CHUNK_MIN, g->E >> 12));
     for (uint32_t u = 0; u < V;) {
         const uint32_t first = u, e0 = off[u];
         ++u;
-        while (u < V && u - first < PB_MAXS && off[u + 1] - e0 <= PB_CHUNK_E) ++u;
+        while (u < V && u - first < PB_MAXS && off[u + 1] - e0 <= chunk_e) ++u;
         if (off[u] != e0) chunks.push_back(make_uint2(first, u - first));
     }
     const uint32_t nC = (uint32_t)chunks.size();
