@@ -39,7 +39,7 @@ struct DevCtl {
     unsigned int done;      // 0 running, 1 halted, 2 superstep cap reached
     unsigned int err;       // device-side error bits
     unsigned int prev_bcast;
-    unsigned int pad0;
+    unsigned int pr_stale;  // PageRank: the broadcasts of the last superstep were not written (blocked pull)
     unsigned long long t_prev;  // %globaltimer at the previous selector call
 };
 

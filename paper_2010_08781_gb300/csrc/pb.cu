@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(PB1_THREADS) k_pb_scatter(Params P) {
     __shared__ uint32_t task, next_win;
     const PbDev& B = P.pb;
     const uint32_t s = P.ctl->superstep;  // the superstep being computed
-    const float* cur = (s & 1) ? P.contrib0 : P.contrib1;
+    const bool sent = s - 1 < P.T;        // superstep s-1 broadcast rank / out-degree (Fig. 8)
     const uint32_t lane = threadIdx.x & 31;
     if (blockIdx.x == 0 && threadIdx.x == 0) B.ctr[1] = 0;  // phase 2 of this superstep claims from 0
     for (;;) {
@@ -98,13 +98,19 @@ __global__ void __launch_bounds__(PB1_THREADS) k_pb_scatter(Params P) {
         if (c >= B.n_chunks) break;
         const uint4 ch = B.chunk[c];  // {first source, sources, first run, end run}
         const uint32_t s0 = ch.x, ns = ch.y;
+        // the broadcast of superstep s-1 is its rank / out-degree, formed here from
+        // the rank (the accumulate launch stores only ranks: compute() of a bin then
+        // reads no global memory)
         for (uint32_t i0 = threadIdx.x; i0 < ns; i0 += PB_BATCH * blockDim.x) {  // PB_BATCH loads in flight
-            float x[PB_BATCH];
+            float x[PB_BATCH], iod[PB_BATCH];
 #pragma unroll
             for (int u = 0; u < PB_BATCH; ++u) {
                 const uint32_t i = i0 + u * blockDim.x;
-                x[u] = i < ns ? cur[s0 + i] : 0.0f;
+                x[u] = i < ns ? P.rank[s0 + i] : 0.0f;
+                iod[u] = i < ns ? __ldg(P.inv_outdeg + s0 + i) : 0.0f;
             }
+#pragma unroll
+            for (int u = 0; u < PB_BATCH; ++u) x[u] = sent ? x[u] * iod[u] : 0.0f;  // as pr_finish
 #pragma unroll
             for (int u = 0; u < PB_BATCH; ++u) {
                 const uint32_t i = i0 + u * blockDim.x;
@@ -243,35 +249,21 @@ __device__ __forceinline__ bool pb_mbar_wait(uint32_t bar, uint32_t parity) {
 
 // compute() of the bin's vertices first, first + stride, ... < nv (vertex v0 + v):
 // the sum is hi:lo in 2^-S units, the high word read only where touched marks
-// one (carries and big contributions set it). PB_BATCH vertices' loads are in
-// flight at once. Clears the vertex's high word and low word for the next bin.
-// The rank is stored only in a superstep that can be the run's last (s >= T or
-// the superstep cap): until then only the broadcast is read by anyone.
+// one (carries and big contributions set it). Clears the vertex's high word and
+// low word for the next bin. Stores the rank only: the broadcast rank / out-degree
+// is formed by the next scatter (or by k_pr_contrib before a push or gather
+// superstep), so this loop reads no global memory on the common path.
 __device__ __forceinline__ void pb_finish(const Params& P, uint32_t* hi, uint32_t* lo, const uint32_t* touched,
-                                          uint32_t v0, uint32_t nv, uint32_t first, uint32_t stride, uint32_t s,
-                                          float* nxt, float inv_scale) {
-    const bool last = s >= P.T || s + 1 >= P.max_supersteps;
-    for (uint32_t b = first; b < nv; b += PB_BATCH * stride) {
-        uint32_t h[PB_BATCH];
-        float iod[PB_BATCH];
-#pragma unroll
-        for (int u = 0; u < PB_BATCH; ++u) {
-            const uint32_t v = b + u * stride;
-            const bool t = v < nv && ((touched[v >> 5] >> (v & 31)) & 1u);
-            h[u] = t ? __ldcg(hi + v) : 0u;
-            iod[u] = v < nv ? __ldg(P.inv_outdeg + v0 + v) : 0.0f;
+                                          uint32_t v0, uint32_t nv, uint32_t first, uint32_t stride,
+                                          float inv_scale) {
+    for (uint32_t v = first; v < nv; v += stride) {
+        uint32_t h = 0;
+        if ((touched[v >> 5] >> (v & 31)) & 1u) {
+            h = __ldcg(hi + v);
+            if (h) hi[v] = 0;
         }
-#pragma unroll
-        for (int u = 0; u < PB_BATCH; ++u) {
-            const uint32_t v = b + u * stride;
-            if (v < nv) {
-                if (h[u]) hi[v] = 0;
-                const float r = fmaf(P.damping, pb_value(h[u], lo[v], inv_scale), P.pr_base);  // as pr_finish
-                if (last) P.rank[v0 + v] = r;
-                nxt[v0 + v] = s < P.T ? r * iod[u] : 0.0f;
-                lo[v] = 0;
-            }
-        }
+        P.rank[v0 + v] = fmaf(P.damping, pb_value(h, lo[v], inv_scale), P.pr_base);  // as pr_finish
+        lo[v] = 0;
     }
 }
 
@@ -309,8 +301,6 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
     // bin k is cleared after its compute() while bin k+1 marks the other one
     __shared__ uint32_t touched2[2][PB_BIN_V / 32];
     const PbDev& B = P.pb;
-    const uint32_t s = P.ctl->superstep;
-    float* nxt = (s & 1) ? P.contrib1 : P.contrib0;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = pb_smem(bars), empty0 = pb_smem(bars + PB_STAGES);
     if (threadIdx.x == 0) {
@@ -321,7 +311,10 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
         pb_mbar_init(pb_smem(cbar), PB2_CONSUMERS);
         pb_mbar_init(pb_smem(cbar + 1), PB2_CONSUMERS);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        if (blockIdx.x == 0) B.ctr[0] = 0;  // phase 1 of the next superstep claims from 0
+        if (blockIdx.x == 0) {
+            B.ctr[0] = 0;          // phase 1 of the next superstep claims from 0
+            P.ctl->pr_stale = 1;   // this superstep's broadcasts are not written (see k_pr_contrib)
+        }
     }
     for (uint32_t i = threadIdx.x; i < PB_BIN_V; i += blockDim.x) acc_lo[i] = 0;
     for (uint32_t i = threadIdx.x; i < 2 * (PB_BIN_V / 32); i += blockDim.x) touched2[i / (PB_BIN_V / 32)][i % (PB_BIN_V / 32)] = 0;
@@ -416,7 +409,7 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
             // the barrier also orders the high-word atomics before the reads below
             bool ok = pb_consumer_sync(cb0, bins_done & 1, lane);
             uint32_t* touched = touched2[bins_done & 1];
-            pb_finish(P, hi, acc_lo, touched, m.x, m.y, c, 32 * PB2_CONSUMERS, s, nxt, inv_scale);
+            pb_finish(P, hi, acc_lo, touched, m.x, m.y, c, 32 * PB2_CONSUMERS, inv_scale);
             ok = pb_consumer_sync(cb1, bins_done & 1, lane) && ok;
             // bin k+1 marks the other bitmap; this one is clear before bin k+2 starts
             for (uint32_t i = c; i < PB_BIN_V / 32; i += 32 * PB2_CONSUMERS) touched[i] = 0;

@@ -237,6 +237,7 @@ __global__ void k_pr_init(Params P) {
         c->done = 0;
         c->err = 0;
         c->prev_bcast = 0;
+        c->pr_stale = 0;
         c->t_prev = globaltimer();
     }
 }
@@ -712,6 +713,21 @@ __device__ __forceinline__ void pr_scatter(const Params& P, float x, uint32_t b,
     }
 }
 
+// After a blocked-pull superstep (which stores ranks only), the broadcasts of
+// that superstep for the push and gather exchanges: rank / out-degree while it
+// was < T. Nothing when the last superstep wrote them itself.
+__global__ void __launch_bounds__(BLOCK) k_pr_contrib(Params P) {
+    if (!P.ctl->pr_stale) return;
+    const uint32_t sp = P.ctl->superstep - 1;
+    float* cur = (sp & 1) ? P.contrib1 : P.contrib0;
+    const bool sent = sp < P.T;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < P.V; v += gridDim.x * blockDim.x)
+        cur[v] = sent ? P.rank[v] * P.inv_outdeg[v] : 0.0f;  // as pr_finish
+}
+
+// Clears the flag of k_pr_contrib once every CTA has read it.
+__global__ void k_pr_contrib_done(Params P) { P.ctl->pr_stale = 0; }
+
 __global__ void __launch_bounds__(BLOCK) k_pr_push(Params P) {
     const uint32_t sp = P.ctl->superstep - 1;  // deliver the broadcasts of superstep sp
     const float* cur = (sp & 1) ? P.contrib1 : P.contrib0;
@@ -889,9 +905,14 @@ int launch_superstep(const ip_graph* g, const Params& P, int mode, cudaStream_t 
     };
     mark(0);
     if (P.app == APP_PR) {
+        const bool blocked = mode == IP_MODE_PULL && P.pb.on;
+        if (!blocked && P.pb.on) {  // the last superstep may have been a blocked pull: its broadcasts
+            k_pr_contrib<<<G[G_MISC], BLOCK, 0, st>>>(P);
+            k_pr_contrib_done<<<1, 1, 0, st>>>(P);
+        }
         mark(1);
         if (mode == IP_MODE_PULL) {
-            if (P.pb.on) {
+            if (blocked) {
                 const int r = pb_launch(g, P, st);
                 if (r != IP_OK) return r;
             } else {
