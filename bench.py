@@ -401,7 +401,7 @@ def pr_measure(G, V, E, reps=3, T=30, engine="auto"):
             "ms": round(min(ts), 4), "ms_per_iteration": round(min(ts) / T, 4),
             "roofline": {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": peak,
                          "peak_kind": kind, "unit": "GB/s", "frac": round(ach / peak, 4),
-                         "traffic": measured_traffic(kern) if E >= 1 << 30 else None,
+                         "traffic": measured_traffic(kern) if E >= 10**9 else None,  # captured at scale 26
                          "avg_launch_us": round(1e3 * avg, 2), "bytes_per_launch": by}}
 
 

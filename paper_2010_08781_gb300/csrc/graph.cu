@@ -10,6 +10,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -186,46 +187,89 @@ static int bin_alloc(ip_graph* g, BinSet* S, int k, int i, size_t bytes) {
     return r;
 }
 
-// Static degree bins of one direction, built on the host from the offsets.
-static int build_bins(ip_graph* g, BinSet* S, int k, const uint32_t* dev_off, cudaStream_t st) {
-    const uint32_t n = g->V, t1 = S->t1, t2 = S->t2;
-    std::vector<uint32_t> off((size_t)n + 1);
-    CK(cudaMemcpyAsync(off.data(), dev_off, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    std::vector<uint32_t> med;
-    std::vector<uint4> chunks;
-    std::vector<uint2> hv;
-    for (uint32_t v = 0; v < n; ++v) {
-        const uint32_t b = off[v], e = off[v + 1], d = e - b;
-        if (d > t1 && d < t2) {
-            med.push_back(v);
-        } else if (d >= t2) {
+// Degree bins on the device. Counting pass: medium vertices (t1 < deg < t2), heavy
+// vertices (deg >= t2) and their chunks of at most HCH edges, warp-aggregated.
+__global__ void k_bin_count(const uint32_t* __restrict__ off, uint32_t n, uint32_t t1, uint32_t t2, uint32_t* cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t wbase = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u, wstride = gridDim.x * blockDim.x;
+    uint32_t med = 0, hv = 0, ch = 0;
+    for (uint32_t v0 = wbase; v0 < n; v0 += wstride) {  // the same trip count for the 32 lanes of a warp
+        const uint32_t v = v0 + lane;
+        const uint32_t d = v < n ? off[v + 1] - off[v] : 0u;
+        med += (d > t1 && d < t2) ? 1u : 0u;
+        if (d >= t2) {
+            ++hv;
+            ch += (d + HCH - 1) / HCH;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        med += __shfl_xor_sync(0xFFFFFFFFu, med, o);
+        hv += __shfl_xor_sync(0xFFFFFFFFu, hv, o);
+        ch += __shfl_xor_sync(0xFFFFFFFFu, ch, o);
+    }
+    if (lane == 0) {
+        if (med) atomicAdd(cnt, med);
+        if (hv) atomicAdd(cnt + 1, hv);
+        if (ch) atomicAdd(cnt + 2, ch);
+    }
+}
+
+// Filling pass (cnt = cursors from 0): the medium list, and per heavy vertex its
+// table entry {first chunk, chunks} and its chunks {vertex, first edge, end edge,
+// heavy-vertex index} in edge order (the PageRank finish sums partials in that order).
+__global__ void k_bin_fill(const uint32_t* __restrict__ off, uint32_t n, uint32_t t1, uint32_t t2, uint32_t* cnt,
+                           uint32_t* med, uint4* chunks, uint2* hvert) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t wbase = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u, wstride = gridDim.x * blockDim.x;
+    for (uint32_t v0 = wbase; v0 < n; v0 += wstride) {
+        const uint32_t v = v0 + lane;
+        const uint32_t b = v < n ? off[v] : 0u, e = v < n ? off[v + 1] : 0u, d = e - b;
+        const bool is_med = d > t1 && d < t2;
+        const uint32_t mask = __ballot_sync(0xFFFFFFFFu, is_med);
+        uint32_t base = 0;
+        if (lane == 0 && mask) base = atomicAdd(cnt, (uint32_t)__popc(mask));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (is_med) med[base + __popc(mask & ((1u << lane) - 1u))] = v;
+        if (d >= t2) {
             const uint32_t nch = (d + HCH - 1) / HCH;
-            hv.push_back(make_uint2((uint32_t)chunks.size(), nch));
+            const uint32_t hi = atomicAdd(cnt + 1, 1u), c0 = atomicAdd(cnt + 2, nch);
+            hvert[hi] = make_uint2(c0, nch);
             for (uint32_t c = 0; c < nch; ++c) {
                 const uint32_t cb = b + c * HCH;
-                const uint32_t ce = (e - cb) > HCH ? cb + HCH : e;
-                chunks.push_back(make_uint4(v, cb, ce, (uint32_t)hv.size() - 1));
+                chunks[c0 + c] = make_uint4(v, cb, (e - cb) > HCH ? cb + HCH : e, hi);
             }
         }
     }
+}
+
+// Static degree bins of one direction, built on the device from the offsets;
+// the host reads back only the three list sizes.
+static int build_bins(ip_graph* g, BinSet* S, int k, const uint32_t* dev_off, cudaStream_t st) {
+    const uint32_t n = g->V, t1 = S->t1, t2 = S->t2;
+    uint32_t* cnt = g->bin_cnt;  // [3], device
+    CK(cudaMemsetAsync(cnt, 0, 3 * sizeof(uint32_t), st));
+    const int grid = std::max(1, std::min(g->num_sms * 8, (int)(((uint64_t)n + 255) / 256)));
+    k_bin_count<<<grid, 256, 0, st>>>(dev_off, n, t1, t2, cnt);
+    CK(cudaGetLastError());
+    uint32_t h[3];
+    CK(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     Bins& B = S->b[k];
     void** mem = S->mem[k];
     int r;
-    const size_t sz[5] = {med.size() * 4, chunks.size() * 16, hv.size() * 8, hv.size() * 4, chunks.size() * 8};
+    const size_t sz[5] = {(size_t)h[0] * 4, (size_t)h[2] * 16, (size_t)h[1] * 8, (size_t)h[1] * 4, (size_t)h[2] * 8};
     for (int i = 0; i < 5; ++i)
         if ((r = bin_alloc(g, S, k, i, sz[i]))) return r;
-    if (!med.empty()) CK(cudaMemcpyAsync(mem[0], med.data(), sz[0], cudaMemcpyHostToDevice, st));
-    if (!chunks.empty()) CK(cudaMemcpyAsync(mem[1], chunks.data(), sz[1], cudaMemcpyHostToDevice, st));
-    if (!hv.empty()) CK(cudaMemcpyAsync(mem[2], hv.data(), sz[2], cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(cnt, 0, 3 * sizeof(uint32_t), st));
+    k_bin_fill<<<grid, 256, 0, st>>>(dev_off, n, t1, t2, cnt, (uint32_t*)mem[0], (uint4*)mem[1], (uint2*)mem[2]);
+    CK(cudaGetLastError());
     CK(cudaMemsetAsync(mem[3], 0, sz[3] ? sz[3] : 16, st));
-    CK(cudaStreamSynchronize(st));
     B.med = (const uint32_t*)mem[0];
-    B.n_med = (uint32_t)med.size();
+    B.n_med = h[0];
     B.hchunk = (const uint4*)mem[1];
-    B.n_hchunk = (uint32_t)chunks.size();
+    B.n_hchunk = h[2];
     B.hvert = (const uint2*)mem[2];
-    B.n_hvert = (uint32_t)hv.size();
+    B.n_hvert = h[1];
     B.hcnt = (uint32_t*)mem[3];
     B.hpart = (float2*)mem[4];
     return IP_OK;
@@ -327,6 +371,7 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
     int r;
     // control block first: validation uses its error word
     if ((r = alloc_dev(g, (void**)&g->ctl, sizeof(DevCtl)))) return r;
+    if ((r = alloc_dev(g, (void**)&g->bin_cnt, 4 * sizeof(uint32_t)))) return r;
     CK(cudaMemsetAsync(g->ctl, 0, sizeof(DevCtl), st));
     CK(cudaMallocHost((void**)&g->ctl_host, sizeof(DevCtl)));
 
@@ -453,7 +498,8 @@ void ip_graph_destroy(ip_graph_t* g) {
     void* bufs[] = {g->ctl,        g->csr_off,    g->csr_col, g->csr_w,      g->inv_outdeg, g->value,
                     g->rank,       g->contrib[0], g->contrib[1], g->mbox,  g->mboxf,      g->recv, g->outbox,
                     g->bcast[0],   g->bcast[1],   g->rq,      g->log,        g->sel,        g->snap_value,
-                    g->q[0][0],    g->q[0][1],    g->q[1][0], g->q[1][1],    g->hq[0],      g->hq[1]};
+                    g->q[0][0],    g->q[0][1],    g->q[1][0], g->q[1][1],    g->hq[0],      g->hq[1],
+                    g->bin_cnt};
     for (void* p : bufs)
         if (p) cudaFree(p);
     for (BinSet* S : g->binsets) free_binset(g, S);

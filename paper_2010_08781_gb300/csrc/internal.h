@@ -222,6 +222,7 @@ struct ip_graph {
     void* batch = nullptr;        // state of the batched runs (batch.cu)
     uint32_t* track_send = nullptr;  // when set, runs record per-vertex last sends here (batched Hashmin)
     void* pb = nullptr;              // blocked PageRank pull layout (pb.cu), built on first use
+    uint32_t* bin_cnt = nullptr;     // [3] device counters of the degree-bin builder
 };
 
 namespace ipg {

@@ -2,13 +2,16 @@
 
 The blocked engine computes the same PULL exchange as the CSC gather (every
 vertex sums its in-neighbours' broadcasts, Fig. 8) through a second edge layout:
-per-chunk runs of entries grouped by destination bin, summed in shared memory in
-64-bit fixed point. The bar is the one of every PageRank path: max relative error
-1e-5 per vertex of the FP64 oracle. The graphs below reach every structural case
-of the layout: bins split into several phase-2 pieces (more than 2^20 entries
-into one bin of 24,576 vertices), runs longer than one record (2,048 entries), a
-single source with more out-edges than a chunk's target (131,072), chunks cut by
-their source count (16,384), sources without out-edges, and a partial last bin.
+runs of entries from a chunk of sources into a bin of destinations, the sources'
+broadcasts written next to the entries as fixed-point codes, and every bin summed
+exactly in shared memory. The bar is the one of every PageRank path: max relative
+error 1e-5 per vertex of the FP64 oracle. The graphs below reach every structural
+case of the layout: a single source with more out-edges than a chunk's target (a
+chunk of one source), a destination with more in-edges than a bin's target (a bin
+of few vertices), runs padded to 4 entries, chunks cut by their source count,
+long stretches of sources without out-edges, partial bins, codes of 2^31 units or
+more (the high word of the sums), and mode sequences that switch between the
+blocked pull and the push exchange (broadcasts rebuilt from ranks).
 """
 import numpy as np
 import pytest
@@ -43,9 +46,9 @@ def _blocked(G, **kw):
 
 
 def _hub_graph():
-    """An out-hub of 300,000 edges (one chunk of one source, runs of 24,576 entries
-    split into records), an in-hub of 1.2M edges (a bin of more than 2^20 entries,
-    split into pieces), sources without out-edges, and an ER background."""
+    """An out-hub of 300,000 edges (a chunk of one source, long runs), an in-hub of
+    1.2M edges (a bin of few vertices), sources without out-edges, and an ER
+    background."""
     n = 1_300_000
     rng = np.random.default_rng(7)
     out_src = np.zeros(300_000, np.uint32)
@@ -124,7 +127,7 @@ def test_hubs_split_bins_and_long_runs():
 
 
 def test_rmat20_and_determinism():
-    g = inputs.rmat_graph(20, seed=1)  # bin 0 receives about a fifth of the 16M edges: several pieces
+    g = inputs.rmat_graph(20, seed=1)  # 16M edges: hundreds of chunks and bins
     want, _ = _ref(g)
     with ipg.Graph.from_inputs(g) as G:
         _, a = _blocked(G)
