@@ -288,6 +288,16 @@ int ip_mlp_pack(const float* params, const float* mu_sd, void* blob, void* strea
 int ip_hashmin_noalloc(uint32_t n_vertices, uint64_t n_edges, const uint32_t* csr_offsets, const uint32_t* csr_cols,
                        uint32_t* labels, uint32_t max_supersteps, uint32_t* supersteps_out, void* stream);
 
+/* Device memory. A graph's device buffers come from a process-wide cache kept by
+ * the library: ip_graph_destroy synchronises the graph's device and returns the
+ * buffers to the cache (at most 32 GiB stay cached), and an allocation of the same
+ * size on the same device reuses one, so building graphs of the same shape again
+ * and again allocates once. An allocation that fails releases the cache of its
+ * device and retries. The paper has no counterpart (its graphs are built once).
+ * ip_release_cached_memory frees every cached buffer on every device and returns
+ * IP_OK; the cache is guarded by a lock, so any thread may call it. */
+int ip_release_cached_memory(void);
+
 /* Human-readable text for an IP_* code (static storage). */
 const char* ip_strerror(int code);
 

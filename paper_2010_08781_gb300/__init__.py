@@ -76,7 +76,7 @@ class GraphInfo(ctypes.Structure):
 _lib = None
 
 # every symbol include/ipregel.h declares
-EXPORTS = ("ip_options_default", "ip_graph_create", "ip_graph_destroy", "ip_graph_info", "ip_run", "ip_get_values",
+EXPORTS = ("ip_options_default", "ip_release_cached_memory", "ip_graph_create", "ip_graph_destroy", "ip_graph_info", "ip_run", "ip_get_values",
            "ip_set_selector", "ip_strerror", "ip_hashmin_noalloc", "ip_mlp_workspace_bytes", "ip_mlp_forward",
            "ip_mlp_backward", "ip_mlp_adam", "ip_mlp_pack", "ip_run_batch_sssp", "ip_run_batch_hashmin")
 BATCH_MAX_SOURCES = 256
@@ -129,6 +129,8 @@ def load(build_if_missing: bool = True):
     L.ip_run_batch_hashmin.restype = ctypes.c_int
     L.ip_strerror.argtypes = [ctypes.c_int]
     L.ip_strerror.restype = ctypes.c_char_p
+    L.ip_release_cached_memory.argtypes = []
+    L.ip_release_cached_memory.restype = ctypes.c_int
     for name in ("ip_graph_create", "ip_graph_info", "ip_run", "ip_get_values", "ip_set_selector"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -177,6 +179,11 @@ def tuned_defaults() -> dict:
         p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_defaults.json")
         _TUNED = json.load(open(p)) if os.path.exists(p) else {}
     return _TUNED
+
+
+def release_cached_memory():
+    """Frees the device buffers the library keeps cached from destroyed graphs."""
+    _check(load().ip_release_cached_memory(), "ip_release_cached_memory")
 
 
 def default_options(app=None, **kw) -> Options:

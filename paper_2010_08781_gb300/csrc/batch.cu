@@ -604,7 +604,7 @@ int ensure_small(ip_graph* g, BatchState* b, size_t words) {
         if (r) return r;
     }
     if (b->small_cap < words) {
-        if (b->small) cudaFree(b->small);
+        if (b->small) free_dev(b->small);
         b->small = nullptr;
         b->small_cap = 0;
         int r = alloc_dev(g, (void**)&b->small, words * 4);
@@ -616,7 +616,7 @@ int ensure_small(ip_graph* g, BatchState* b, size_t words) {
 
 int ensure_out(ip_graph* g, BatchState* b, size_t words) {
     if (b->out_cap >= words) return IP_OK;
-    if (b->out_tmp) cudaFree(b->out_tmp);
+    if (b->out_tmp) free_dev(b->out_tmp);
     b->out_tmp = nullptr;
     b->out_cap = 0;
     int r = alloc_dev(g, (void**)&b->out_tmp, words * 4);
@@ -718,7 +718,7 @@ void free_batch_state(ip_graph* g) {
     drop_exec(b);
     void* bufs[] = {b->dist, b->mbox, b->masks, b->tasks, b->small, b->msgs, b->state, b->bar, b->out_tmp, b->track};
     for (void* p : bufs)
-        if (p) cudaFree(p);
+        if (p) free_dev(p);
     delete b;
     g->batch = nullptr;
 }
@@ -742,7 +742,7 @@ int ip_run_batch_sssp(ip_graph_t* g, const uint32_t* sources, uint32_t k, uint32
     int r;
     if (b->ms_G != G) {  // per-vertex storage for G groups of 32 sources
         for (void* p : {(void*)b->dist, (void*)b->mbox, (void*)b->masks}) {
-            if (p) cudaFree(p);
+            if (p) free_dev(p);
         }
         g->device_bytes -= b->bytes;
         b->dist = b->mbox = b->masks = nullptr;

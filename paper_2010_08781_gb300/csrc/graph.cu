@@ -11,7 +11,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -30,16 +33,100 @@ int cuda_err(cudaError_t e) {
         if (_r != IP_OK) return _r;        \
     } while (0)
 
+// Process-wide cache of the library's device buffers, by device and exact size.
+// ip_graph_destroy returns a graph's buffers here (after one device
+// synchronisation) instead of freeing them, and the next allocation of the same
+// size on the same device takes one back: a caller that builds graphs of the same
+// shape again and again pays cudaMalloc / cudaFree (which synchronises) once. At
+// most DEV_CACHE_CAP bytes stay cached; an allocation that fails first releases
+// the cache of its device; ip_release_cached_memory() releases everything.
+namespace {
+constexpr size_t DEV_CACHE_CAP = 32ull << 30;
+struct DeviceCache {
+    std::mutex m;
+    std::unordered_map<void*, std::pair<int, size_t>> live;   // buffers handed out: device, size
+    std::multimap<std::pair<int, size_t>, void*> cached;      // returned buffers, by (device, size)
+    size_t cached_bytes = 0;
+};
+DeviceCache& dcache() {
+    static DeviceCache* c = new DeviceCache();  // never destroyed: no ordering problem at process exit
+    return *c;
+}
+
+// Frees the cached buffers of one device (dev < 0: of every device). Caller holds the lock.
+void dcache_trim_locked(DeviceCache& C, int dev) {
+    int cur = -1;
+    (void)cudaGetDevice(&cur);
+    for (auto it = C.cached.begin(); it != C.cached.end();) {
+        if (dev >= 0 && it->first.first != dev) {
+            ++it;
+            continue;
+        }
+        (void)cudaSetDevice(it->first.first);
+        cudaFree(it->second);
+        C.cached_bytes -= it->first.second;
+        it = C.cached.erase(it);
+    }
+    if (cur >= 0) (void)cudaSetDevice(cur);
+}
+
+// Hands a library buffer back to the cache (the device has been synchronised).
+void dcache_release(void* p) {
+    if (!p) return;
+    DeviceCache& C = dcache();
+    std::lock_guard<std::mutex> l(C.m);
+    auto it = C.live.find(p);
+    if (it == C.live.end()) {
+        cudaFree(p);
+        return;
+    }
+    const std::pair<int, size_t> key = it->second;
+    C.live.erase(it);
+    if (C.cached_bytes + key.second <= DEV_CACHE_CAP) {
+        C.cached.insert({key, p});
+        C.cached_bytes += key.second;
+    } else {
+        cudaFree(p);
+    }
+}
+}  // namespace
+
 int alloc_dev(ip_graph* g, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        (void)cudaGetLastError();
-        return e == cudaErrorMemoryAllocation ? IP_E_NOMEM : IP_E_CUDA;
+    DeviceCache& C = dcache();
+    std::lock_guard<std::mutex> l(C.m);
+    auto it = C.cached.find({g->device, bytes});
+    if (it != C.cached.end()) {
+        *p = it->second;
+        C.cached.erase(it);
+        C.cached_bytes -= bytes;
+    } else {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaErrorMemoryAllocation && C.cached_bytes) {
+            (void)cudaGetLastError();
+            dcache_trim_locked(C, g->device);
+            e = cudaMalloc(p, bytes);
+        }
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            (void)cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? IP_E_NOMEM : IP_E_CUDA;
+        }
     }
+    C.live[*p] = {g->device, bytes};
     g->device_bytes += bytes;
     return IP_OK;
+}
+
+// Frees a library buffer now (mid-run frees: bin sets, regrown logs, build temporaries).
+void free_dev(void* p) {
+    if (!p) return;
+    DeviceCache& C = dcache();
+    {
+        std::lock_guard<std::mutex> l(C.m);
+        C.live.erase(p);
+    }
+    cudaFree(p);
 }
 
 static size_t edge_alloc_count(uint64_t E) { return (size_t)(((E + 3) & ~3ull) + 4); }
@@ -137,7 +224,7 @@ static int exclusive_scan(ip_graph* g, uint32_t* data, uint64_t n, cudaStream_t 
         r = cuda_err(cudaGetLastError());
     }
     cudaStreamSynchronize(st);
-    cudaFree(sums);
+    free_dev(sums);
     return r;
 }
 
@@ -174,7 +261,7 @@ static void free_binset(ip_graph* g, BinSet* S) {
     for (int k = 0; k < 2; ++k)
         for (int i = 0; i < 5; ++i)
             if (S->mem[k][i]) {
-                cudaFree(S->mem[k][i]);
+                free_dev(S->mem[k][i]);
                 g->device_bytes -= S->bytes[k][i];
             }
     delete S;
@@ -315,7 +402,7 @@ int ensure_bins(ip_graph* g, uint32_t t1, uint32_t t2, cudaStream_t st) {
         free_graph_exec(g);
         for (int p = 0; p < 2; ++p)
             if (g->hq[p]) {
-                cudaFree(g->hq[p]);
+                free_dev(g->hq[p]);
                 g->device_bytes -= (size_t)(g->hq_cap + 1) * sizeof(uint2);
                 g->hq[p] = nullptr;
             }
@@ -417,7 +504,7 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
         }
         cudaError_t e1 = cudaGetLastError();
         cudaError_t e2 = cudaStreamSynchronize(st);
-        cudaFree(cursor);
+        free_dev(cursor);
         CK(e1);
         CK(e2);
     }
@@ -492,6 +579,10 @@ void ip_options_default(ip_options_t* o) {
 
 void ip_graph_destroy(ip_graph_t* g) {
     if (!g) return;
+    int cur = -1;
+    (void)cudaGetDevice(&cur);
+    (void)cudaSetDevice(g->device);
+    (void)cudaDeviceSynchronize();  // no kernel uses the buffers below any more: they can be cached
     free_graph_exec(g);
     free_batch_state(g);
     pb_free(g);
@@ -500,19 +591,26 @@ void ip_graph_destroy(ip_graph_t* g) {
                     g->bcast[0],   g->bcast[1],   g->rq,      g->log,        g->sel,        g->snap_value,
                     g->q[0][0],    g->q[0][1],    g->q[1][0], g->q[1][1],    g->hq[0],      g->hq[1],
                     g->bin_cnt};
-    for (void* p : bufs)
-        if (p) cudaFree(p);
+    for (void* p : bufs) dcache_release(p);
     for (BinSet* S : g->binsets) free_binset(g, S);
     g->binsets.clear();
     if (!g->csc_alias) {
-        if (g->csc_off) cudaFree(g->csc_off);
-        if (g->csc_row) cudaFree(g->csc_row);
-        if (g->csc_w) cudaFree(g->csc_w);
+        dcache_release(g->csc_off);
+        dcache_release(g->csc_row);
+        dcache_release(g->csc_w);
     }
     if (g->ctl_host) cudaFreeHost(g->ctl_host);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     delete g;
+    if (cur >= 0) (void)cudaSetDevice(cur);
+}
+
+int ip_release_cached_memory(void) {
+    DeviceCache& C = dcache();
+    std::lock_guard<std::mutex> l(C.m);
+    dcache_trim_locked(C, -1);
+    return IP_OK;
 }
 
 int ip_graph_create(ip_graph_t** out, uint32_t n_vertices, uint64_t n_edges, const uint32_t* csr_offsets,

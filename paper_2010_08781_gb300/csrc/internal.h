@@ -228,6 +228,7 @@ struct ip_graph {
 namespace ipg {
 // graph.cu
 int alloc_dev(ip_graph* g, void** p, size_t bytes);
+void free_dev(void* p);
 int ensure_bins(ip_graph* g, uint32_t t1, uint32_t t2, cudaStream_t st);
 int cuda_err(cudaError_t e);
 // batch.cu

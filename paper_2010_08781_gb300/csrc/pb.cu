@@ -576,7 +576,7 @@ int pb_alloc(ip_graph* g, PbLayout* L, T** p, size_t count) {
 
 void pb_release(ip_graph* g, PbLayout* L) {
     for (auto& b : L->bufs) {
-        cudaFree(b.first);
+        free_dev(b.first);
         g->device_bytes -= b.second;
     }
     delete L;
@@ -589,7 +589,7 @@ struct TmpBuf {
     size_t bytes = 0;
     ~TmpBuf() {
         if (p) {
-            cudaFree(p);
+            free_dev(p);
             g->device_bytes -= bytes;
         }
     }

@@ -1213,7 +1213,7 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     const uint32_t want_log = std::min<uint32_t>(max_supersteps, 1u << 16);
     if (g->log_cap < want_log) {
         if (g->log) {
-            cudaFree(g->log);
+            free_dev(g->log);
             g->device_bytes -= (size_t)g->log_cap * sizeof(LogRec);
         }
         g->log = nullptr;
