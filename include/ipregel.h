@@ -176,6 +176,22 @@ void ip_graph_destroy(ip_graph_t* g);
 
 int ip_graph_info(const ip_graph_t* g, ip_graph_info_t* info);
 
+/* Renumbers the graph's vertices inside the handle by decreasing out-degree
+ * class (class = floor(log2 out-degree), vertices without out-edges last; the
+ * original order is kept inside a class), on the device. The paper keeps the
+ * caller's numbering (Section 4.2); the renumbering only changes where a vertex's
+ * state sits in memory, so that the high-degree vertices the pull exchanges gather
+ * from share cache lines. It is invisible through the ABI: sources, instance
+ * offsets, Hashmin labels (smallest CALLER id of the component), distances and
+ * ranks stay in the caller's numbering, and every result is the one of the graph
+ * as given. Costs: two n_vertices uint32 maps, one more copy of the edges while it
+ * runs, and a gather on every ip_get_values. Every cached state of the handle
+ * (degree bins, run graphs, blocked-engine layout, batched-run state) is rebuilt;
+ * the values of a previous run are dropped (IP_E_STATE until the next run).
+ * A second call is a no-op. Returns IP_E_NOMEM (the handle is then unusable and
+ * must only be destroyed) or IP_E_CUDA on failure. Synchronises the stream. */
+int ip_graph_relabel(ip_graph_t* g, void* stream);
+
 /* Runs one application to global halt (Section 4.2: the run ends when every
  * vertex has voted to halt and no message is in flight) or until
  * max_supersteps supersteps (superstep 0 included) have run, whichever comes

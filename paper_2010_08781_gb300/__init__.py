@@ -78,10 +78,11 @@ _lib = None
 # every symbol include/ipregel.h declares
 EXPORTS = ("ip_options_default", "ip_release_cached_memory", "ip_graph_create", "ip_graph_destroy", "ip_graph_info", "ip_run", "ip_get_values",
            "ip_set_selector", "ip_strerror", "ip_hashmin_noalloc", "ip_mlp_workspace_bytes", "ip_mlp_forward",
-           "ip_mlp_backward", "ip_mlp_adam", "ip_mlp_pack", "ip_run_batch_sssp", "ip_run_batch_hashmin")
+           "ip_mlp_backward", "ip_mlp_adam", "ip_mlp_pack", "ip_run_batch_sssp", "ip_run_batch_hashmin", "ip_graph_relabel")
 BATCH_MAX_SOURCES = 256
 MLP_PARAMS = 32 * 8 + 32 + 32 * 32 + 32 + 3 * 32 + 3
 NOALLOC_MAX_VERTICES = 1 << 20
+RELABEL_AUTO_EDGES = 1 << 20  # graphs this large are renumbered by degree class unless asked otherwise
 
 
 def lib_path() -> str:
@@ -106,6 +107,7 @@ def load(build_if_missing: bool = True):
     L.ip_graph_destroy.argtypes = [vp]
     L.ip_graph_destroy.restype = None
     L.ip_graph_info.argtypes = [vp, ctypes.POINTER(GraphInfo)]
+    L.ip_graph_relabel.argtypes = [vp, vp]
     L.ip_run.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(Options), ctypes.POINTER(RunStatsC)]
     L.ip_get_values.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int, vp]
     L.ip_set_selector.argtypes = [vp, vp, ctypes.c_size_t]
@@ -236,9 +238,12 @@ class Graph:
     """A graph resident on the current CUDA device (owns its device memory)."""
 
     def __init__(self, n, csr_offsets, csr_cols, csr_weights=None, csc_offsets=None, csc_rows=None,
-                 csc_weights=None, symmetric=False, stream=None, selector="default"):
+                 csc_weights=None, symmetric=False, stream=None, selector="default", relabel="auto"):
         """selector: "default" loads the trained selector shipped with the package
-        (if present), None loads nothing, bytes load that blob."""
+        (if present), None loads nothing, bytes load that blob.
+        relabel: True renumbers the vertices inside the handle by degree class
+        (ip_graph_relabel; results keep the caller's numbering), False keeps the
+        given numbering, "auto" renumbers graphs of at least RELABEL_AUTO_EDGES edges."""
         L = load()
         self._h = ctypes.c_void_p()
         arrays = [csr_offsets, csr_cols, csr_weights, csc_offsets, csc_rows, csc_weights]
@@ -256,6 +261,11 @@ class Graph:
         st = _stream_handle(stream)
         _check(L.ip_graph_create(ctypes.byref(self._h), self.n, m, *p, device_ptrs, st), "ip_graph_create")
         self._keep = None  # the library copied everything
+        self.relabeled = False
+        if relabel == "auto":
+            relabel = m >= RELABEL_AUTO_EDGES
+        if relabel:
+            self.relabel(stream)
         if selector == "default":
             from .selector import load_default_blob
             selector = load_default_blob()
@@ -263,13 +273,19 @@ class Graph:
             self.set_selector(selector)
 
     @classmethod
-    def from_inputs(cls, g, stream=None, build_csc_on_device=False, selector="default"):
+    def from_inputs(cls, g, stream=None, build_csc_on_device=False, selector="default", relabel="auto"):
         """From an inputs.Graph (host numpy arrays)."""
+        kw = dict(stream=stream, selector=selector, relabel=relabel)
         if g.symmetric:
-            return cls(g.n, g.row_ptr, g.col, g.w, symmetric=True, stream=stream, selector=selector)
+            return cls(g.n, g.row_ptr, g.col, g.w, symmetric=True, **kw)
         if build_csc_on_device:
-            return cls(g.n, g.row_ptr, g.col, g.w, stream=stream, selector=selector)
-        return cls(g.n, g.row_ptr, g.col, g.w, g.t_ptr, g.t_idx, g.wt, stream=stream, selector=selector)
+            return cls(g.n, g.row_ptr, g.col, g.w, **kw)
+        return cls(g.n, g.row_ptr, g.col, g.w, g.t_ptr, g.t_idx, g.wt, **kw)
+
+    def relabel(self, stream=None):
+        """Renumber the vertices inside the handle by degree class (ip_graph_relabel)."""
+        _check(load().ip_graph_relabel(self._h, _stream_handle(stream)), "ip_graph_relabel")
+        self.relabeled = True
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -347,7 +347,9 @@ __global__ void __launch_bounds__(BB) k_msssp(MsParams P) {
 }
 
 // dist[v][G][32] -> out[k][v] for k < K (source-major), 32x32 tiles through shared memory.
-__global__ void k_ms_transpose(const uint32_t* dist, uint32_t V, uint32_t G, uint32_t K, uint32_t* out) {
+// On a renumbered graph v runs over the caller's ids and reads internal row nid[v].
+__global__ void k_ms_transpose(const uint32_t* dist, uint32_t V, uint32_t G, uint32_t K, const uint32_t* nid,
+                               uint32_t* out) {
     __shared__ uint32_t tile[32][33];
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const uint32_t vt = (V + 31) / 32;
@@ -355,7 +357,7 @@ __global__ void k_ms_transpose(const uint32_t* dist, uint32_t V, uint32_t G, uin
         const uint32_t v0 = (t / G) * 32, g = t % G;
         for (uint32_t j = wib; j < 32; j += blockDim.x >> 5) {
             const uint32_t v = v0 + j;
-            tile[j][lane] = v < V ? dist[slot(v, G, g) + lane] : INF;
+            tile[j][lane] = v < V ? dist[slot(nid ? __ldg(nid + v) : v, G, g) + lane] : INF;
         }
         __syncthreads();
         for (uint32_t j = wib; j < 32; j += blockDim.x >> 5) {
@@ -364,6 +366,11 @@ __global__ void k_ms_transpose(const uint32_t* dist, uint32_t V, uint32_t G, uin
         }
         __syncthreads();
     }
+}
+
+// Caller's source ids -> internal ids, in place.
+__global__ void k_map_ids(uint32_t* ids, uint32_t k, const uint32_t* nid) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) ids[i] = nid[ids[i]];
 }
 
 // =================================================================== multi-instance Hashmin
@@ -378,7 +385,9 @@ struct BhParams {
     uint32_t* outbox;  // label if broadcast in the last superstep, else INF
     uint32_t* mbox;
     uint32_t* recv;
-    const uint32_t* inst_off;  // k+1 vertex offsets of the instances
+    const uint32_t* inst_off;  // k+1 vertex offsets of the instances (caller's ids)
+    const uint32_t* orig;      // renumbered graph: internal id -> caller's id, else null
+    const uint32_t* nid;       // renumbered graph: caller's id -> internal id, else null
     uint32_t k;
     uint32_t* inst_last;       // [k]: last superstep in which the instance sent a message
     unsigned long long* msgs;
@@ -400,6 +409,8 @@ __device__ __forceinline__ uint32_t instance_of(const BhParams& P, uint32_t v) {
     return lo;
 }
 
+__device__ __forceinline__ uint32_t caller_id(const BhParams& P, uint32_t v) { return P.orig ? __ldg(P.orig + v) : v; }
+
 __device__ __forceinline__ void bh_fold(const BhParams& P, uint32_t b, uint32_t e, uint32_t pos, uint32_t stride,
                                         uint32_t& m, bool& any) {
     for (uint32_t ei = b + pos; ei < e; ei += stride) {
@@ -418,12 +429,13 @@ __global__ void __launch_bounds__(BB) k_bhashmin(BhParams P) {
     // superstep 0 (Fig. 9): label = id, every vertex broadcasts
     unsigned long long sent0 = 0;
     for (uint32_t v = tid; v < P.V; v += nth) {
-        P.label[v] = v;
-        P.outbox[v] = v;
+        const uint32_t id = caller_id(P, v);
+        P.label[v] = id;
+        P.outbox[v] = id;
         P.mbox[v] = INF;
         const uint32_t d = P.csr_off[v + 1] - P.csr_off[v];
         sent0 += d;
-        if (d) P.inst_last[instance_of(P, v)] = 0;
+        if (d) P.inst_last[instance_of(P, id)] = 0;
     }
     for (uint32_t w = tid; w < P.W; w += nth) P.recv[w] = 0;
     const unsigned long long t0 = block_sum(sent0);
@@ -506,7 +518,7 @@ __global__ void __launch_bounds__(BB) k_bhashmin(BhParams P) {
                     out = m;
                     const uint32_t d = P.csr_off[v + 1] - P.csr_off[v];
                     mine += d;
-                    if (d) P.inst_last[instance_of(P, v)] = s;
+                    if (d) P.inst_last[instance_of(P, caller_id(P, v))] = s;
                 }
             }
             if (v < P.V) P.outbox[v] = out;
@@ -522,10 +534,10 @@ __global__ void __launch_bounds__(BB) k_bhashmin(BhParams P) {
     }
 }
 
-// Union labels -> labels local to each instance.
+// Union labels -> labels local to each instance, in the caller's numbering.
 __global__ void k_bh_local(const BhParams P, uint32_t* out) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < P.V; v += gridDim.x * blockDim.x)
-        out[v] = P.label[v] - __ldg(P.inst_off + instance_of(P, v));
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P.V; u += gridDim.x * blockDim.x)
+        out[u] = P.label[P.nid ? __ldg(P.nid + u) : u] - __ldg(P.inst_off + instance_of(P, u));
 }
 
 // Engine 0 helpers: per-instance maximum of the per-vertex last-send record
@@ -778,6 +790,10 @@ int ip_run_batch_sssp(ip_graph_t* g, const uint32_t* sources, uint32_t k, uint32
     }
     if ((r = ensure_small(g, b, 2 * (size_t)G * 32))) return r;
     CKB(cudaMemcpyAsync(b->small, sources, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    if (g->new_of_old) {
+        k_map_ids<<<(k + 255) / 256, 256, 0, st>>>(b->small, k, g->new_of_old);
+        CKB(cudaGetLastError());
+    }
     CKB(cudaMemsetAsync(b->msgs, 0, 4 * sizeof(unsigned long long), st));
     CKB(cudaMemsetAsync(b->bar, 0, sizeof(GridBar), st));
 
@@ -822,7 +838,7 @@ int ip_run_batch_sssp(ip_graph_t* g, const uint32_t* sources, uint32_t k, uint32
         out = b->out_tmp;
     }
     const uint32_t tiles = ((g->V + 31) / 32) * G;
-    k_ms_transpose<<<std::min<uint32_t>(tiles, (uint32_t)g->num_sms * 8), 256, 0, st>>>(b->dist, g->V, G, k, out);
+    k_ms_transpose<<<std::min<uint32_t>(tiles, (uint32_t)g->num_sms * 8), 256, 0, st>>>(b->dist, g->V, G, k, g->new_of_old, out);
     CKB(cudaGetLastError());
     if (!out_is_device)
         CKB(cudaMemcpyAsync(dist_out, out, (size_t)k * g->V * 4, cudaMemcpyDeviceToHost, st));
@@ -865,14 +881,24 @@ int ip_run_batch_hashmin(ip_graph_t* g, const uint32_t* instance_offsets, uint32
         g->track_send = nullptr;
         if (r != IP_OK && r != IP_E_MAXSTEPS) return r;
         uint32_t* inst_last = b->small + k + 1;
-        k_inst_max<<<std::min<uint32_t>(k, (uint32_t)g->num_sms * 8), BB, 0, st>>>(b->track, b->small, k, inst_last);
+        const uint32_t* label = g->value;
+        const uint32_t* track = b->track;
+        if (g->new_of_old) {  // per-vertex records back to the caller's numbering
+            int r2;  // r keeps the run's own status
+            if (!g->snap_value && (r2 = alloc_dev(g, (void**)&g->snap_value, (size_t)g->V * 8))) return r2;
+            if ((r2 = unpermute(g, g->value, g->snap_value, st))) return r2;
+            if ((r2 = unpermute(g, b->track, g->snap_value + g->V, st))) return r2;
+            label = g->snap_value;
+            track = g->snap_value + g->V;
+        }
+        k_inst_max<<<std::min<uint32_t>(k, (uint32_t)g->num_sms * 8), BB, 0, st>>>(track, b->small, k, inst_last);
         uint32_t* out = labels_out;
         if (!out_is_device) {
             int r2 = ensure_out(g, b, g->V);
             if (r2) return r2;
             out = b->out_tmp;
         }
-        k_local_labels<<<g->num_sms * 8, 256, 0, st>>>(g->value, g->V, b->small, k, out);
+        k_local_labels<<<g->num_sms * 8, 256, 0, st>>>(label, g->V, b->small, k, out);
         CKB(cudaGetLastError());
         if (!out_is_device) CKB(cudaMemcpyAsync(labels_out, out, (size_t)g->V * 4, cudaMemcpyDeviceToHost, st));
         if (stats) {
@@ -911,6 +937,8 @@ int ip_run_batch_hashmin(ip_graph_t* g, const uint32_t* instance_offsets, uint32
     P.mbox = g->mbox;
     P.recv = g->recv;
     P.inst_off = b->small;
+    P.orig = g->old_of_new;
+    P.nid = g->new_of_old;
     P.k = k;
     P.inst_last = b->small + k + 1;
     P.msgs = b->msgs;

@@ -118,9 +118,21 @@ int alloc_dev(ip_graph* g, void** p, size_t bytes) {
     return IP_OK;
 }
 
+// While set on a thread, free_dev hands buffers to the cache instead of freeing
+// them: the caller has synchronised the device, so no launch still reads them.
+static thread_local bool t_device_idle = false;
+struct DeviceIdleScope {
+    DeviceIdleScope() { t_device_idle = true; }
+    ~DeviceIdleScope() { t_device_idle = false; }
+};
+
 // Frees a library buffer now (mid-run frees: bin sets, regrown logs, build temporaries).
 void free_dev(void* p) {
     if (!p) return;
+    if (t_device_idle) {
+        dcache_release(p);
+        return;
+    }
     DeviceCache& C = dcache();
     {
         std::lock_guard<std::mutex> l(C.m);
@@ -446,6 +458,41 @@ static int upload(ip_graph* g, uint32_t** dst, const uint32_t* src, size_t count
     return IP_OK;
 }
 
+// The CSC of g's CSR, transposed on the device (count, scan, scatter); the order
+// of a vertex's in-edges is unspecified.
+static int transpose_csr(ip_graph* g, cudaStream_t st) {
+    const uint32_t n = g->V;
+    const uint64_t E = g->E;
+    const size_t ea = edge_alloc_count(E);
+    int r;
+    if ((r = alloc_dev(g, (void**)&g->csc_off, ((size_t)n + 1) * sizeof(uint32_t)))) return r;
+    if ((r = alloc_dev(g, (void**)&g->csc_row, ea * sizeof(uint32_t)))) return r;
+    CK(cudaMemsetAsync(g->csc_row + E, 0, (ea - E) * sizeof(uint32_t), st));  // the padding after the last edge
+    if (g->csr_w) {
+        if ((r = alloc_dev(g, (void**)&g->csc_w, ea * sizeof(uint32_t)))) return r;
+        CK(cudaMemsetAsync(g->csc_w + E, 0, (ea - E) * sizeof(uint32_t), st));
+    }
+    CK(cudaMemsetAsync(g->csc_off, 0, ((size_t)n + 1) * sizeof(uint32_t), st));
+    if (E) {
+        k_count_in<<<grid_for(g, E), 256, 0, st>>>(g->csr_col, E, g->csc_off);
+        CK(cudaGetLastError());
+    }
+    if ((r = exclusive_scan(g, g->csc_off, (uint64_t)n + 1, st))) return r;
+    uint32_t* cursor = nullptr;
+    if ((r = alloc_dev(g, (void**)&cursor, (size_t)n * sizeof(uint32_t)))) return r;
+    g->device_bytes -= (size_t)n * sizeof(uint32_t);
+    CK(cudaMemcpyAsync(cursor, g->csc_off, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    if (E)
+        k_scatter_in<<<grid_for(g, E), 256, 0, st>>>(g->csr_off, g->csr_col, g->csr_w, n, E, cursor, g->csc_row,
+                                                      g->csc_w);
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    free_dev(cursor);
+    CK(e1);
+    CK(e2);
+    return IP_OK;
+}
+
 static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, const uint32_t* csr_col,
                   const uint32_t* csr_w, const uint32_t* csc_off, const uint32_t* csc_row, const uint32_t* csc_w,
                   int device_ptrs, cudaStream_t st) {
@@ -479,34 +526,8 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
         if ((r = upload(g, &g->csc_row, csc_row, E, ea, device_ptrs, st))) return r;
         if (csc_w && (r = upload(g, &g->csc_w, csc_w, E, ea, device_ptrs, st))) return r;
         if ((r = validate_device(g, g->csc_off, g->csc_row, st))) return r;
-    } else {
-        // transpose on the device: count, scan, scatter
-        if ((r = alloc_dev(g, (void**)&g->csc_off, ((size_t)n + 1) * sizeof(uint32_t)))) return r;
-        if ((r = alloc_dev(g, (void**)&g->csc_row, ea * sizeof(uint32_t)))) return r;
-        CK(cudaMemsetAsync(g->csc_row, 0, ea * sizeof(uint32_t), st));
-        if (csr_w) {
-            if ((r = alloc_dev(g, (void**)&g->csc_w, ea * sizeof(uint32_t)))) return r;
-            CK(cudaMemsetAsync(g->csc_w, 0, ea * sizeof(uint32_t), st));
-        }
-        CK(cudaMemsetAsync(g->csc_off, 0, ((size_t)n + 1) * sizeof(uint32_t), st));
-        if (E) {
-            k_count_in<<<grid_for(g, E), 256, 0, st>>>(g->csr_col, E, g->csc_off);
-            CK(cudaGetLastError());
-        }
-        if ((r = exclusive_scan(g, g->csc_off, (uint64_t)n + 1, st))) return r;
-        uint32_t* cursor = nullptr;
-        if ((r = alloc_dev(g, (void**)&cursor, (size_t)n * sizeof(uint32_t)))) return r;
-        g->device_bytes -= (size_t)n * sizeof(uint32_t);
-        CK(cudaMemcpyAsync(cursor, g->csc_off, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
-        if (E) {
-            k_scatter_in<<<grid_for(g, E), 256, 0, st>>>(g->csr_off, g->csr_col, g->csr_w, n, E, cursor, g->csc_row,
-                                                          g->csc_w);
-        }
-        cudaError_t e1 = cudaGetLastError();
-        cudaError_t e2 = cudaStreamSynchronize(st);
-        free_dev(cursor);
-        CK(e1);
-        CK(e2);
+    } else if ((r = transpose_csr(g, st))) {
+        return r;
     }
     if (csr_w && !g->csc_w) return IP_E_INVAL;
 
@@ -553,6 +574,238 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
     return IP_OK;
 }
 
+// ------------------------------------------------------------ vertex renumbering
+// Vertices are renumbered by decreasing out-degree class (class = leading zeros of
+// the degree, degree 0 last), keeping the original order inside a class (a stable
+// counting sort): the sources of the high-degree vertices then share cache lines,
+// so the gathers of the pull exchanges hit L1/L2 more often. The caller's numbering
+// stays the interface: values, sources and instance offsets are mapped at the edge.
+constexpr uint32_t RL_KEYS = 33;
+__device__ __forceinline__ uint32_t rl_key(uint32_t d) { return d ? (uint32_t)__clz(d) : 32u; }
+
+// Per block of consecutive vertices [b*R, (b+1)*R): counts per key.
+__global__ void k_rl_hist(const uint32_t* __restrict__ off, uint32_t n, uint32_t R, uint32_t* hist) {
+    __shared__ uint32_t h[RL_KEYS];
+    for (uint32_t i = threadIdx.x; i < RL_KEYS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const uint64_t v0 = (uint64_t)blockIdx.x * R, v1 = v0 + R < n ? v0 + R : n;
+    for (uint64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) atomicAdd(h + rl_key(off[v + 1] - off[v]), 1u);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < RL_KEYS; i += blockDim.x) hist[(size_t)blockIdx.x * RL_KEYS + i] = h[i];
+}
+
+// One warp per block of vertices, in order: new number = the key's first place
+// for this block (pos) + the rank among the block's earlier vertices of that key.
+__global__ void k_rl_place(const uint32_t* __restrict__ off, uint32_t n, uint32_t R, const uint32_t* __restrict__ pos,
+                           uint32_t* new_of_old, uint32_t* old_of_new, uint32_t* deg_new, uint32_t* start_old) {
+    __shared__ uint32_t cur[RL_KEYS];
+    const uint32_t lane = threadIdx.x;
+    for (uint32_t i = lane; i < RL_KEYS; i += 32) cur[i] = pos[(size_t)blockIdx.x * RL_KEYS + i];
+    __syncwarp();
+    const uint64_t v0 = (uint64_t)blockIdx.x * R, v1 = v0 + R < n ? v0 + R : n;
+    for (uint64_t b = v0; b < v1; b += 32) {  // the same trip count for the 32 lanes
+        const uint64_t v = b + lane;
+        const bool ok = v < v1;
+        const uint32_t d = ok ? off[v + 1] - off[v] : 0u;
+        const uint32_t key = ok ? rl_key(d) : RL_KEYS;
+        const uint32_t same = __match_any_sync(0xFFFFFFFFu, key);
+        const uint32_t leader = __ffs(same) - 1;
+        uint32_t base = 0;
+        if (lane == leader && ok) base = cur[key];
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (ok) {
+            const uint32_t p = base + __popc(same & ((1u << lane) - 1u));
+            new_of_old[v] = p;
+            old_of_new[p] = (uint32_t)v;
+            deg_new[p] = d;
+            start_old[p] = off[v];
+        }
+        __syncwarp();
+        if (lane == leader && ok) cur[key] += __popc(same);
+        __syncwarp();
+    }
+}
+
+// The renumbered CSR, cut into chunks of RL_CH consecutive NEW edge positions, one
+// warp per chunk: the chunk's first source comes from k_rl_chunk_src, the warp holds
+// the first new and old edge positions of 32 consecutive sources in registers, and
+// each lane finds the source of its edge by a binary search over them (shuffles).
+// Writes are coalesced whatever the degrees; the targets are renumbered on the way.
+constexpr uint32_t RL_CH = 1024;
+constexpr uint32_t RL_UNROLL = 4;
+
+// chunk_src[c] = the source of new edge position c * RL_CH (largest s with off_new[s] <= c * RL_CH).
+__global__ void k_rl_chunk_src(const uint32_t* __restrict__ off_new, uint32_t n, uint32_t n_chunks,
+                               uint32_t* chunk_src) {
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_chunks; c += gridDim.x * blockDim.x) {
+        const uint64_t p = (uint64_t)c * RL_CH;
+        uint32_t lo = 0, hi = n;  // off_new[lo] <= p; the answer is below hi
+        while (hi - lo > 1) {
+            const uint32_t mid = lo + (hi - lo) / 2;
+            if (off_new[mid] <= p)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        chunk_src[c] = lo;
+    }
+}
+
+__global__ void k_rl_edges(const uint32_t* __restrict__ off_new, const uint32_t* __restrict__ start_old,
+                           const uint32_t* __restrict__ chunk_src, const uint32_t* __restrict__ col,
+                           const uint32_t* __restrict__ w, const uint32_t* __restrict__ new_of_old, uint32_t n,
+                           uint64_t E, uint32_t n_chunks, uint32_t* __restrict__ col_new, uint32_t* __restrict__ w_new) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += nw) {
+        const uint64_t p0 = (uint64_t)c * RL_CH;
+        const uint64_t p1 = p0 + RL_CH < E ? p0 + RL_CH : E;
+        for (uint64_t s = chunk_src[c];; s += 32) {  // windows of 32 sources
+            const uint64_t sl = s + lane;
+            const uint32_t wo = sl < n ? off_new[sl] : (uint32_t)E;  // the lane's source: first new position
+            const uint32_t ws = sl < n ? start_old[sl] : 0u;         // and first old position
+            const uint64_t wend = s + 32 <= n ? (uint64_t)off_new[s + 32] : E;
+            const uint64_t w0 = __shfl_sync(FULL, wo, 0);
+            const uint64_t lo = p0 > w0 ? p0 : w0, hi = p1 < wend ? p1 : wend;
+            for (uint64_t base = lo; base < hi; base += 32 * RL_UNROLL) {
+                uint32_t q[RL_UNROLL], pos[RL_UNROLL], cv[RL_UNROLL], wv[RL_UNROLL];
+#pragma unroll
+                for (uint32_t u = 0; u < RL_UNROLL; ++u) {
+                    const uint64_t qq = base + 32 * u + lane;
+                    q[u] = qq < hi ? (uint32_t)qq : 0xFFFFFFFFu;
+                    uint32_t i = 0;  // largest i with wo(i) <= q
+#pragma unroll
+                    for (uint32_t step = 16; step; step >>= 1)
+                        if (__shfl_sync(FULL, wo, i + step) <= q[u]) i += step;
+                    pos[u] = __shfl_sync(FULL, ws, i) + (q[u] - __shfl_sync(FULL, wo, i));
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < RL_UNROLL; ++u) {
+                    cv[u] = q[u] != 0xFFFFFFFFu ? col[pos[u]] : 0u;
+                    wv[u] = (w && q[u] != 0xFFFFFFFFu) ? w[pos[u]] : 0u;
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < RL_UNROLL; ++u)
+                    if (q[u] != 0xFFFFFFFFu) {
+                        col_new[q[u]] = new_of_old[cv[u]];
+                        if (w) w_new[q[u]] = wv[u];
+                    }
+            }
+            if (wend >= p1) break;
+        }
+    }
+}
+
+// out[old] = in[new_of_old[old]] (a per-vertex array back to the caller's numbering).
+__global__ void k_rl_unpermute(const uint32_t* __restrict__ in, const uint32_t* __restrict__ new_of_old, uint32_t n,
+                               uint32_t* out) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        out[v] = in[new_of_old[v]];
+}
+
+int unpermute(const ip_graph* g, const uint32_t* in, uint32_t* out, cudaStream_t st) {
+    k_rl_unpermute<<<grid_for(g, g->V), 256, 0, st>>>(in, g->new_of_old, g->V, out);
+    return cuda_err(cudaGetLastError());
+}
+
+static int relabel(ip_graph* g, cudaStream_t st) {
+    if (g->new_of_old) return IP_OK;
+    const uint32_t n = g->V;
+    const uint64_t E = g->E;
+    const size_t ea = edge_alloc_count(E);
+    int r;
+    const uint32_t nblk =
+        (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)g->num_sms * 16, ((uint64_t)n + 255) / 256));
+    const uint32_t R = (uint32_t)(((uint64_t)n + nblk - 1) / nblk);
+    const uint32_t n_chunks = (uint32_t)((E + RL_CH - 1) / RL_CH);
+    uint32_t *hist = nullptr, *pos = nullptr, *off_new = nullptr, *col_new = nullptr, *w_new = nullptr;
+    uint32_t *start_old = nullptr, *chunk_src = nullptr;
+    if ((r = alloc_dev(g, (void**)&g->new_of_old, (size_t)n * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&g->old_of_new, (size_t)n * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&hist, (size_t)nblk * RL_KEYS * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&pos, (size_t)nblk * RL_KEYS * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&off_new, ((size_t)n + 1) * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&start_old, (size_t)n * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&chunk_src, (size_t)n_chunks * 4))) return r;
+    if ((r = alloc_dev(g, (void**)&col_new, ea * 4))) return r;
+    CK(cudaMemsetAsync(col_new + E, 0, (ea - E) * 4, st));  // the padding after the last edge
+    if (g->csr_w) {
+        if ((r = alloc_dev(g, (void**)&w_new, ea * 4))) return r;
+        CK(cudaMemsetAsync(w_new + E, 0, (ea - E) * 4, st));
+    }
+    // stable counting sort of the vertices by key
+    k_rl_hist<<<nblk, 256, 0, st>>>(g->csr_off, n, R, hist);
+    CK(cudaGetLastError());
+    std::vector<uint32_t> h((size_t)nblk * RL_KEYS), p((size_t)nblk * RL_KEYS);
+    CK(cudaMemcpyAsync(h.data(), hist, h.size() * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    uint64_t acc = 0;
+    for (uint32_t k = 0; k < RL_KEYS; ++k)
+        for (uint32_t b = 0; b < nblk; ++b) {
+            p[(size_t)b * RL_KEYS + k] = (uint32_t)acc;
+            acc += h[(size_t)b * RL_KEYS + k];
+        }
+    CK(cudaMemcpyAsync(pos, p.data(), p.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(off_new + n, 0, 4, st));
+    k_rl_place<<<nblk, 32, 0, st>>>(g->csr_off, n, R, pos, g->new_of_old, g->old_of_new, off_new, start_old);
+    CK(cudaGetLastError());
+    if ((r = exclusive_scan(g, off_new, (uint64_t)n + 1, st))) return r;  // out-degrees -> offsets
+    if (E) {
+        k_rl_chunk_src<<<grid_for(g, n_chunks), 256, 0, st>>>(off_new, n, n_chunks, chunk_src);
+        CK(cudaGetLastError());
+        k_rl_edges<<<grid_for(g, (uint64_t)n_chunks * 32), 256, 0, st>>>(
+            off_new, start_old, chunk_src, g->csr_col, g->csr_w, g->new_of_old, n, E, n_chunks, col_new, w_new);
+        CK(cudaGetLastError());
+    }
+    // Every buffer of the old numbering goes back to the device cache (the rebuilt
+    // degree bins have the same sizes and take theirs back): the device is idle first.
+    CK(cudaDeviceSynchronize());
+    const bool alias = g->csc_alias;
+    {
+        DeviceIdleScope idle;
+        free_dev(hist);
+        free_dev(pos);
+        free_dev(start_old);
+        free_dev(chunk_src);
+        g->device_bytes -= (size_t)nblk * RL_KEYS * 8 + (size_t)n * 4 + (size_t)n_chunks * 4;
+        if (!alias) {
+            free_dev(g->csc_off);
+            free_dev(g->csc_row);
+            free_dev(g->csc_w);
+            g->device_bytes -= ((size_t)n + 1) * 4 + ea * 4 * (g->csc_w ? 2 : 1);
+        }
+        free_dev(g->csr_off);
+        free_dev(g->csr_col);
+        free_dev(g->csr_w);
+        g->device_bytes -= ((size_t)n + 1) * 4 + ea * 4 * (g->csr_w ? 2 : 1);
+        free_graph_exec(g);
+        free_batch_state(g);
+        pb_free(g);
+        for (BinSet* S : g->binsets) free_binset(g, S);
+        g->binsets.clear();
+        g->cur = nullptr;
+        g->last_app = -1;
+    }
+    // the renumbered CSR; the CSC is the CSR again (symmetric) or transposed anew
+    g->csr_off = off_new;
+    g->csr_col = col_new;
+    g->csr_w = w_new;
+    g->csc_off = g->csc_row = g->csc_w = nullptr;
+    if (alias) {
+        g->csc_off = g->csr_off;
+        g->csc_row = g->csr_col;
+        g->csc_w = g->csr_w;
+    } else if ((r = transpose_csr(g, st))) {
+        return r;
+    }
+    k_degrees<<<grid_for(g, n), 256, 0, st>>>(g->csr_off, n, g->inv_outdeg, &g->ctl->err);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(&g->ctl->err, 0, 4, st));
+    if ((r = ensure_bins(g, DEFAULT_T1, DEFAULT_T2, st))) return r;
+    CK(cudaStreamSynchronize(st));
+    return IP_OK;
+}
+
 }  // namespace ipg
 
 using namespace ipg;
@@ -583,6 +836,7 @@ void ip_graph_destroy(ip_graph_t* g) {
     (void)cudaGetDevice(&cur);
     (void)cudaSetDevice(g->device);
     (void)cudaDeviceSynchronize();  // no kernel uses the buffers below any more: they can be cached
+    DeviceIdleScope idle;
     free_graph_exec(g);
     free_batch_state(g);
     pb_free(g);
@@ -590,7 +844,7 @@ void ip_graph_destroy(ip_graph_t* g) {
                     g->rank,       g->contrib[0], g->contrib[1], g->mbox,  g->mboxf,      g->recv, g->outbox,
                     g->bcast[0],   g->bcast[1],   g->rq,      g->log,        g->sel,        g->snap_value,
                     g->q[0][0],    g->q[0][1],    g->q[1][0], g->q[1][1],    g->hq[0],      g->hq[1],
-                    g->bin_cnt};
+                    g->bin_cnt,    g->new_of_old, g->old_of_new};
     for (void* p : bufs) dcache_release(p);
     for (BinSet* S : g->binsets) free_binset(g, S);
     g->binsets.clear();
@@ -604,6 +858,11 @@ void ip_graph_destroy(ip_graph_t* g) {
     if (g->ev1) cudaEventDestroy(g->ev1);
     delete g;
     if (cur >= 0) (void)cudaSetDevice(cur);
+}
+
+int ip_graph_relabel(ip_graph_t* g, void* stream) {
+    if (!g) return IP_E_INVAL;
+    return relabel(g, (cudaStream_t)stream);
 }
 
 int ip_release_cached_memory(void) {
@@ -659,6 +918,15 @@ int ip_get_values(ip_graph_t* g, void* dst, size_t dst_bytes, int dst_is_device,
     if (dst_bytes < need) return IP_E_RANGE;
     const void* src = g->last_app == IP_PAGERANK ? (const void*)g->rank : (const void*)g->value;
     cudaStream_t st = (cudaStream_t)stream;
+    if (g->new_of_old) {  // back to the caller's numbering
+        if (!g->snap_value) {
+            int r = alloc_dev(g, (void**)&g->snap_value, (size_t)g->V * 8);
+            if (r) return r;
+        }
+        int r = unpermute(g, (const uint32_t*)src, g->snap_value, st);
+        if (r) return r;
+        src = g->snap_value;
+    }
     CK(cudaMemcpyAsync(dst, src, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return IP_OK;

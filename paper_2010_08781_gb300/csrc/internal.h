@@ -142,6 +142,7 @@ struct Params {
     int32_t use_graph;
     cudaGraphConditionalHandle h_while, h_switch;
     PbDev pb;
+    const uint32_t* orig;  // renumbered graph: internal id -> caller's id (Hashmin labels are caller ids), else null
 };
 
 // PageRank compute() of superstep s (Fig. 8): rank from the sum of the received
@@ -223,6 +224,8 @@ struct ip_graph {
     uint32_t* track_send = nullptr;  // when set, runs record per-vertex last sends here (batched Hashmin)
     void* pb = nullptr;              // blocked PageRank pull layout (pb.cu), built on first use
     uint32_t* bin_cnt = nullptr;     // [3] device counters of the degree-bin builder
+    uint32_t* new_of_old = nullptr;  // renumbered graph (ip_graph_relabel): caller's id -> internal id
+    uint32_t* old_of_new = nullptr;  // internal id -> caller's id
 };
 
 namespace ipg {
@@ -238,6 +241,7 @@ int pb_prepare(ip_graph* g, cudaStream_t st, PbDev* out);
 int pb_launch(const ip_graph* g, const Params& P, cudaStream_t st);
 bool pb_supported(const ip_graph* g);
 void pb_free(ip_graph* g);
+int unpermute(const ip_graph* g, const uint32_t* in, uint32_t* out, cudaStream_t st);
 // superstep.cu
 int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* opt, ip_run_stats_t* stats);
 void free_graph_exec(ip_graph* g);

@@ -162,7 +162,7 @@ __global__ void k_init_min(Params P) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     const bool hm = P.app == APP_HM;
     for (uint32_t v = tid; v < P.V; v += nth) {
-        const uint32_t x = hm ? v : (v == P.source ? 0u : INF);
+        const uint32_t x = hm ? (P.orig ? P.orig[v] : v) : (v == P.source ? 0u : INF);
         P.value[v] = x;
         P.outbox[v] = x;  // every initial value below INF is broadcast
         P.mbox[v] = INF;
@@ -1265,6 +1265,9 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     P.app = (uint32_t)app;
     P.T = o.pr_iterations;
     P.source = o.source;
+    P.orig = g->old_of_new;
+    if (app == APP_SSSP && g->new_of_old)  // the caller's source id -> internal id
+        CKR(cuda_err(cudaMemcpyAsync(&P.source, g->new_of_old + o.source, 4, cudaMemcpyDeviceToHost, st)));
     P.max_supersteps = max_supersteps;
     P.damping = o.damping;
     P.pr_base = (float)((1.0 - (double)o.damping) / (double)g->V);
@@ -1275,7 +1278,8 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     P.max_out_deg = g->max_out_deg;
     if (app == APP_SSSP) {
         uint32_t two[2];
-        CKR(cuda_err(cudaMemcpyAsync(two, g->csr_off + o.source, 8, cudaMemcpyDeviceToHost, st)));
+        CKR(cuda_err(cudaStreamSynchronize(st)));
+        CKR(cuda_err(cudaMemcpyAsync(two, g->csr_off + P.source, 8, cudaMemcpyDeviceToHost, st)));
         CKR(cuda_err(cudaStreamSynchronize(st)));
         P.out_deg_src = two[1] - two[0];
     }
