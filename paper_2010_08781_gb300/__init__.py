@@ -188,13 +188,16 @@ def release_cached_memory():
     _check(load().ip_release_cached_memory(), "ip_release_cached_memory")
 
 
-def default_options(app=None, **kw) -> Options:
-    """Options with the library defaults, the autotuned cutoffs for `app`, then kw."""
+def default_options(app=None, relabeled=True, **kw) -> Options:
+    """Options with the library defaults, the autotuned cutoffs for `app` (tuned on
+    graphs renumbered by degree class, or in the caller's order when relabeled is
+    False: the best cutoffs differ), then kw."""
     o = Options()
     load().ip_options_default(ctypes.byref(o))
     t = tuned_defaults()
-    if app is not None and app in t.get("bins", {}):
-        o.t1, o.t2 = t["bins"][app]["t1"], t["bins"][app]["t2"]
+    bins = t.get("bins", {}) if relabeled else t.get("bins_caller_order", t.get("bins", {}))
+    if app is not None and app in bins:
+        o.t1, o.t2 = bins[app]["t1"], bins[app]["t2"]
     if "modes" in t:
         o.thr_sparse, o.thr_pull = t["modes"]["thr_sparse"], t["modes"]["thr_pull"]
     seq = kw.pop("mode_sequence", None)
@@ -209,6 +212,11 @@ def default_options(app=None, **kw) -> Options:
         if k == "stream" and v is not None and not isinstance(v, int):
             v = v.cuda_stream  # torch.cuda.Stream
         setattr(o, k, v)
+    # a cutoff given alone keeps the tuned other one only where the pair stays ordered (t1 < t2)
+    if "t2" in kw and "t1" not in kw and o.t2 and o.t1 >= o.t2:
+        o.t1 = o.t2 - 1
+    if "t1" in kw and "t2" not in kw and o.t1 and o.t2 and o.t2 <= o.t1:
+        o.t2 = o.t1 + 1
     if seq is not None:
         buf = (ctypes.c_uint8 * len(seq))(*[MODES[m] if isinstance(m, str) else int(m) for m in seq])
         o.mode_sequence = ctypes.cast(buf, ctypes.POINTER(ctypes.c_uint8))
@@ -312,7 +320,7 @@ class Graph:
     def run(self, app, max_supersteps=100000, stats_capacity=1024, raise_on_maxsteps=False, **opts) -> RunStats:
         name = app if isinstance(app, str) else {v: k for k, v in APPS.items()}[int(app)]
         app = APPS[name]
-        o = default_options(name, **opts)
+        o = default_options(name, relabeled=self.relabeled, **opts)
         cap = stats_capacity
         arr = dict(mode=np.zeros(cap, np.uint8), active=np.zeros(cap, np.uint32),
                    broadcasters=np.zeros(cap, np.uint32), messages=np.zeros(cap, np.uint64),

@@ -6,6 +6,10 @@ search of whole runs (device time, median of repeats) on seeded R-MAT graphs.
 Mode cutoffs: the threshold rule's two cutoffs on messages/E are fitted to
 per-superstep timings of all three exchange modes (the selector's label logs).
 
+Both cutoff sets are tuned twice: on graphs renumbered by degree class (the
+binding's default from 2^20 edges) and in the caller's order; the binding picks the
+set that matches the graph.
+
 Command line (on a GPU machine):
     python -m paper_2010_08781_gb300.autotune --out FILE
 The result is written as JSON; the package applies paper_2010_08781_gb300/tuned_defaults.json
@@ -22,7 +26,7 @@ import numpy as np
 
 from . import Graph
 
-T1S = (8, 16, 32, 64)
+T1S = (8, 16, 32, 64, 128)
 T2S = (256, 512, 1024, 2048, 4096)
 
 
@@ -38,14 +42,16 @@ def time_run(G, app, reps, **kw):
     return statistics.median(ts)
 
 
-def tune_bins(reps=3, log=print):
-    """Grid search of (t1, t2) per app; total time over the tuning graphs."""
+def tune_bins(reps=3, relabel=True, log=print):
+    """Grid search of (t1, t2) per app; total time over the tuning graphs, stored
+    renumbered by degree class (relabel=True) or in the caller's order."""
     totals = {app: {} for app in ("hashmin", "sssp", "pagerank")}
     for name, g in _graphs():
-        with Graph.from_inputs(g) as G:
+        with Graph.from_inputs(g, relabel=relabel) as G:
             apps = ("pagerank",) if name.endswith("d") else ("hashmin", "sssp")
             for app in apps:
-                kw = dict(policy="forced", forced_mode="pull") if app == "pagerank" else {}
+                # the degree bins schedule the CSC gather engine (the blocked engine has its own layout)
+                kw = dict(policy="forced", forced_mode="pull", pr_engine="gather") if app == "pagerank" else {}
                 for t1 in T1S:
                     for t2 in T2S:
                         G.run(app, t1=t1, t2=t2, **kw)  # warm-up (bins rebuilt for the new cutoffs)
@@ -75,14 +81,15 @@ def main():
     args = ap.parse_args()
     t0 = time.time()
     bins = tune_bins(args.reps)
+    bins_caller = tune_bins(args.reps, relabel=False)
     modes = tune_modes()
-    res = {"bins": bins, "modes": modes, "seconds": round(time.time() - t0, 1),
+    res = {"bins": bins, "bins_caller_order": bins_caller, "modes": modes, "seconds": round(time.time() - t0, 1),
            "graphs": "R-MAT scale 20/22 symmetrised weighted (seed 3) for Hashmin/SSSP, directed scale 22 for PageRank; "
                      "mode cutoffs from per-mode superstep timings on R-MAT scale 20/22, a in {.45,.57,.65}, seed 5"}
     with open(args.out, "w") as f:
         json.dump(res, f, indent=1)
-    print(json.dumps({k: ({a: {kk: vv for kk, vv in v.items() if kk != "grid_ms"} for a, v in res["bins"].items()}
-                          if k == "bins" else v) for k, v in res.items()}))
+    print(json.dumps({k: ({a: {kk: vv for kk, vv in v.items() if kk != "grid_ms"} for a, v in res[k].items()}
+                          if k.startswith("bins") else v) for k, v in res.items()}))
 
 
 if __name__ == "__main__":

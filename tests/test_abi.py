@@ -51,3 +51,15 @@ def test_create_rejects_bad_arguments_on_host():
                                None) in (ipg.IP_E_INVAL, ipg.IP_E_RANGE)
     assert lib.ip_run(None, 0, 10, None, None) == ipg.IP_E_INVAL
     assert lib.ip_get_values(None, None, 0, 0, None) == ipg.IP_E_INVAL
+
+
+def test_single_cutoff_override_keeps_the_pair_ordered():
+    """A caller who sets one degree-bin cutoff gets the tuned other one only while
+    t1 < t2 still holds; both given are passed through as they are."""
+    for app in ("hashmin", "sssp", "pagerank"):
+        o = ipg.default_options(app, t2=4)
+        assert o.t2 == 4 and o.t1 < 4
+        o = ipg.default_options(app, t1=100000)
+        assert o.t1 == 100000 and o.t2 > 100000
+    o = ipg.default_options("hashmin", t1=10, t2=5)
+    assert (o.t1, o.t2) == (10, 5)  # rejected by ip_run with IP_E_INVAL
