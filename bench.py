@@ -226,9 +226,12 @@ def run_gpu(args, rank, world, local_rank):
     # ---------------------------------------------------------- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
     kern = {}  # name -> [total ms, total bytes, launches]
+    # the timed runs' own mode sequences are replayed (the learned selector reads the
+    # last superstep's time, which events and profilers change)
+    seqs = {app: per_app[app][-1].mode[1:per_app[app][-1].supersteps].tolist() for app in ("hashmin", "sssp")}
     for _ in range(args.steps):
         for app in ("hashmin", "sssp"):
-            st = G.run(app, profile_kernels=1, **opts)
+            st = G.run(app, profile_kernels=1, stream=stream, mode_sequence=seqs[app])
             for s in range(1, st.supersteps):
                 mode = int(st.mode[s])
                 name = KERNEL_NAMES[(MODE_NAMES[mode], app)]
