@@ -9,6 +9,9 @@ leg, and by nothing else. The GPU product path never imports this package.
   Section 4.3.3) running PageRank (Fig. 8 with the Pregel constant of
   Fig. 12), Hashmin (Fig. 9) and weighted SSSP (Fig. 10 with per-edge
   weights). PageRank runs in FP64.
+* ``pagerank_update`` — compute() of Fig. 8 for chosen vertices in one superstep,
+  from the ranks of the superstep before (FP64 numpy): checks a single superstep
+  of a run too large for the full oracle, one vertex at a time.
 * ``mlp.py`` — FP64 forward/backward of the 8-32-32-3 mode-selector MLP.
 
 The compiled part is built on first use with gcc (``build()``).
@@ -144,3 +147,18 @@ def batch_sssp(g, sources, **kw):
 def batch_hashmin(graphs):
     """Hashmin on each graph separately: list of label arrays (local vertex IDs)."""
     return [hashmin(h.n, h.row_ptr, h.col)[0] for h in graphs]
+
+
+def pagerank_update(vertices, n, in_ptr, in_src, out_degree, prev_rank, damping=0.85):
+    """One superstep s >= 1 of PageRank (Fig. 8) for the given vertices: every
+    in-neighbour u broadcast prev_rank[u] / out_degree[u] in superstep s - 1 (Fig.
+    8 sends rank / number of out-neighbours), and the vertex takes (1 - d)/N (the
+    constant of Fig. 12) plus d times the sum of what it received. in_ptr/in_src
+    are the in-edge (transposed) arrays. FP64; returns rank[len(vertices)]."""
+    prev = np.asarray(prev_rank, np.float64)
+    deg = np.asarray(out_degree, np.float64)
+    out = np.empty(len(vertices), np.float64)
+    for i, v in enumerate(vertices):
+        us = np.asarray(in_src[int(in_ptr[v]):int(in_ptr[v + 1])], np.int64)
+        out[i] = (1.0 - damping) / n + damping * float(np.sum(prev[us] / deg[us]))
+    return out

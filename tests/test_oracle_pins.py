@@ -314,3 +314,30 @@ def test_pagerank_cap_stops_early():
     g = inputs.directed_cycle(4)
     r, st = oracle.pagerank(g.n, g.row_ptr, g.col, T=30, max_supersteps=5)
     assert st["supersteps"] == 5 and not st["halted"]
+
+
+def test_pagerank_update_exact_fractions():
+    """The one-superstep update against exact rationals: from a non-uniform rank
+    vector with a dangling in-neighbour, a self-loop and a vertex with no in-edges."""
+    edges = [(0, 1), (0, 2), (1, 2), (2, 0), (2, 3), (4, 2), (3, 3)]
+    n, d = 5, Fraction(85, 100)
+    g = inputs.from_edges(n, [a for a, _ in edges], [b for _, b in edges])
+    outd = [sum(1 for a, _ in edges if a == v) for v in range(n)]
+    prev = [Fraction(k + 1, 17) for k in range(n)]
+    want = [(1 - d) / n] * n
+    for a, b in edges:
+        want[b] += d * prev[a] / outd[a]
+    got = oracle.pagerank_update(range(n), n, g.t_ptr, g.t_idx, g.out_degree(), [float(x) for x in prev])
+    np.testing.assert_allclose(got, [float(x) for x in want], rtol=1e-15)
+
+
+@pytest.mark.parametrize("name", ["rmat10", "er"])
+def test_pagerank_update_iterated_is_the_engine(name):
+    """T updates of every vertex from 1/N reproduce the synchronous engine's run."""
+    g = inputs.rmat_graph(10, seed=4) if name == "rmat10" else inputs.er_graph(500, 1500, seed=5)
+    r = np.full(g.n, 1.0 / g.n)
+    for _ in range(12):
+        r = oracle.pagerank_update(range(g.n), g.n, g.t_ptr, g.t_idx, g.out_degree(), r)
+    want, _ = oracle.pagerank(g.n, g.row_ptr, g.col, T=12)
+    np.testing.assert_allclose(r, want, rtol=1e-12)
+    assert (g.out_degree() == 0).any()
