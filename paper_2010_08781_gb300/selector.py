@@ -128,9 +128,14 @@ class Trainer:
         return bytes(out.cpu().numpy().tobytes())
 
 
-def normalisation(X):
+def normalisation(X, masked=()):
+    """Per-feature mean and spread; a masked feature gets mean 0 and spread 1e30, so
+    its normalised input is ~0 in training and in the engine alike (the network
+    ignores it without a change of the blob layout)."""
     mu = X.mean(axis=0).astype(np.float32)
     sd = (X.std(axis=0) + 1e-3).astype(np.float32)
+    for i in masked:
+        mu[i], sd[i] = 0.0, 1e30
     return mu, sd
 
 
@@ -240,6 +245,8 @@ def main():
     ap.add_argument("--out", default=".")
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--mask", type=int, nargs="*", default=[],
+                    help="feature indices the network ignores (e.g. 5: the last superstep's time)")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     Xtr, Ttr, meta_tr = collect_many(training_graphs())
@@ -247,7 +254,7 @@ def main():
     np.savez_compressed(os.path.join(args.out, "selector_logs.npz"), Xtr=Xtr, Ttr=Ttr, Xev=Xev, Tev=Tev)
     y, w = labels_of(Ttr)
     thr_sparse, thr_pull = tune_threshold(Xtr, Ttr)
-    mu, sd = normalisation(Xtr)
+    mu, sd = normalisation(Xtr, args.mask)
     tr = Trainer(mu, sd)
     t0 = time.time()
     hist = tr.fit(Xtr, y, w, steps=args.steps, lr=args.lr)
@@ -260,6 +267,7 @@ def main():
     rep = {
         "network": "8-32-32-3 MLP, BF16 weights, FP32 accumulation",
         "features": FEATURES,
+        "masked_features": [FEATURES[i] for i in args.mask],
         "training_graphs": training_graphs(),
         "evaluation_graphs": evaluation_graphs(),
         "train_steps": args.steps, "lr": args.lr, "train_seconds": round(train_s, 2), "loss_history": hist,
