@@ -67,28 +67,46 @@ def measured_peaks():
 
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of SM clock and throttle reasons every INTERVAL_MS, started
+    before the warm-up; summary() keeps the samples whose timestamps fall inside the
+    marked timed region (or the nearest one when the region is shorter than the
+    sampling interval)."""
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, device_index):
+        import tempfile
         self.idx = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        fd, self.path = tempfile.mkstemp(prefix=f"ipregel_clocks{device_index}_", suffix=".csv")
+        os.close(fd)
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
-                                         stderr=subprocess.DEVNULL)
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        deadline = time.time() + 5.0  # wait for the first sample
+        while time.time() < deadline and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
         return self
+
+    def start(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
 
     def __exit__(self, *a):
         if self.proc is not None:
+            time.sleep(2 * self.INTERVAL_MS / 1e3)  # a sample after the region
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -96,28 +114,47 @@ class ClockSampler:
                 self.proc.kill()
             self.f.close()
 
+    def _rows(self):
+        from datetime import datetime
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 10:
+                continue
+            try:
+                t = datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((t, float(p[2]), float(p[3]), p))
+            except ValueError:
+                continue
+        return rows
+
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append((float(parts[1]), float(parts[2]), parts))
-            except ValueError:
-                continue
+        rows = self._rows()
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        window = "timed region"
+        sel = rows
+        if self.t0 is not None and self.t1 is not None:
+            sel = [r for r in rows if self.t0 <= r[0] <= self.t1]
+            if not sel:  # region shorter than the interval: the first sample after its start
+                after = [r for r in rows if r[0] >= self.t0]
+                sel = after[:1] or rows[-1:]
+                window = "nearest sample after the start of the timed region"
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for _, _, p in rows:
-            for n, v in zip(names, p[5:9]):
+        for _, _, _, p in sel:
+            for n, v in zip(names, p[6:10]):
                 if v.lower() in ("active", "1"):
                     reasons.add(n)
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": sorted(reasons), "samples": len(rows)}
+        return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": max(r[2] for r in sel),
+                "reasons": sorted(reasons), "samples": len(sel), "window": window,
+                "power_w_median": statistics.median(float(r[3][4]) for r in sel) if sel else None}
 
 
 # ----------------------------------------------------------------- kernel byte models
@@ -195,6 +232,7 @@ def run_gpu(args, rank, world, local_rank):
         b = G.run("sssp", source=0, **opts)
         return a, b
 
+    clk = ClockSampler(local_rank).__enter__()  # sampling from before the warm-up
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -206,7 +244,8 @@ def run_gpu(args, rank, world, local_rank):
     msgs = 0
     launches = 0
     per_app = {"hashmin": [], "sssp": []}
-    with ClockSampler(local_rank) as clk:
+    clk.start()
+    try:
         for i in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()  # evict the previous step's working set from L2 (outside the timed events)
@@ -219,6 +258,9 @@ def run_gpu(args, rank, world, local_rank):
             per_app["hashmin"].append(a)
             per_app["sssp"].append(b)
         torch.cuda.synchronize()
+    finally:
+        clk.stop()
+        clk.__exit__(None, None, None)
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     total_ms, msgs_all = reduce_over_ranks(sum(step_ms), msgs, world, dev)
     value = msgs_all / (total_ms * 1e-3) / 1e9
@@ -476,7 +518,7 @@ def run_config(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--scale", type=int, default=SCALE)

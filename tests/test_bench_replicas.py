@@ -55,3 +55,40 @@ def test_reference_arm_prints_one_line(capsys, monkeypatch):
     bench.main()
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_clock_summary_keeps_the_timed_region(tmp_path):
+    """The clock record of a bench line comes from the samples taken inside the timed
+    region; throttle reasons active there are reported, those outside are not."""
+    import time as _time
+    from datetime import datetime
+
+    import bench
+
+    def line(t, mhz, hw="Not Active"):
+        ts = datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {mhz}, 2070, 900.5, 0x0, {hw}, Not Active, Not Active, Not Active\n"
+
+    c = bench.ClockSampler(0)
+    c.proc = object()  # sampling "ran"
+    t0 = _time.time()
+    with open(c.path, "w") as f:
+        f.write(line(t0 - 1.0, 1000, "Active"))  # before the region: ignored
+        f.write(line(t0 + 0.10, 2070))
+        f.write(line(t0 + 0.20, 2055))
+        f.write(line(t0 + 0.30, 2070))
+        f.write(line(t0 + 2.0, 900, "Active"))  # after the region: ignored
+    c.t0, c.t1 = t0, t0 + 0.35
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070 and s["reasons"] == []
+    assert s["window"] == "timed region"
+
+    c = bench.ClockSampler(0)
+    c.proc = object()
+    with open(c.path, "w") as f:
+        f.write(line(t0 - 1.0, 1000))
+        f.write(line(t0 + 0.5, 2040, "Active"))
+    c.t0, c.t1 = t0, t0 + 0.01  # shorter than the sampling interval
+    s = c.summary()
+    assert s["samples"] == 1 and s["sm_mhz"] == 2040 and s["reasons"] == ["hw_slowdown"]
+    assert s["window"].startswith("nearest")
