@@ -63,3 +63,17 @@ def test_single_cutoff_override_keeps_the_pair_ordered():
         assert o.t1 == 100000 and o.t2 > 100000
     o = ipg.default_options("hashmin", t1=10, t2=5)
     assert (o.t1, o.t2) == (10, 5)  # rejected by ip_run with IP_E_INVAL
+
+
+def test_tuned_cutoffs_follow_the_vertex_order():
+    """Graphs renumbered by degree class and graphs in the caller's order have their
+    own tuned degree-bin cutoffs; the binding picks the set that matches."""
+    t = ipg.tuned_defaults()
+    if "bins_caller_order" not in t:
+        pytest.skip("no tuned cutoffs shipped")
+    for app in ("hashmin", "sssp", "pagerank"):
+        a = ipg.default_options(app)
+        b = ipg.default_options(app, relabeled=False)
+        assert (a.t1, a.t2) == (t["bins"][app]["t1"], t["bins"][app]["t2"])
+        assert (b.t1, b.t2) == (t["bins_caller_order"][app]["t1"], t["bins_caller_order"][app]["t2"])
+        assert a.t1 < a.t2 and b.t1 < b.t2
