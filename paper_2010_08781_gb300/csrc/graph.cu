@@ -1,5 +1,6 @@
 // Graph store: creation (validation, upload, device-side transposition),
-// degree bins, value readback, selector upload and the small ABI helpers.
+// vertex renumbering by degree class, degree bins, value readback, selector
+// upload, the process-wide device-buffer cache and the small ABI helpers.
 //
 // The paper keeps one global vertex array and one global adjacency array
 // shared by all threads (Section 4.2). Here the adjacency is held twice on the
