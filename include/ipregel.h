@@ -189,7 +189,8 @@ int ip_graph_info(const ip_graph_t* g, ip_graph_info_t* info);
  * (degree bins, run graphs, blocked-engine layout, batched-run state) is rebuilt;
  * the values of a previous run are dropped (IP_E_STATE until the next run).
  * A second call is a no-op. Returns IP_E_NOMEM (the handle is then unusable and
- * must only be destroyed) or IP_E_CUDA on failure. Synchronises the stream. */
+ * must only be destroyed) or IP_E_CUDA on failure. Synchronises the device (the
+ * buffers of the old numbering go back to the library's cache). */
 int ip_graph_relabel(ip_graph_t* g, void* stream);
 
 /* Runs one application to global halt (Section 4.2: the run ends when every
