@@ -341,3 +341,22 @@ def test_pagerank_update_iterated_is_the_engine(name):
     want, _ = oracle.pagerank(g.n, g.row_ptr, g.col, T=12)
     np.testing.assert_allclose(r, want, rtol=1e-12)
     assert (g.out_degree() == 0).any()
+
+
+@pytest.mark.parametrize("scale", [12, 14])
+def test_pagerank_sparse_power_iteration(scale):
+    """At R-MAT scale (self-loops, dangling vertices, hubs): T = 30 steps of
+    r <- (1-d)/N + d * A^T (D^+ r) with scipy's sparse matrix product."""
+    g = inputs.rmat_graph(scale, seed=7)
+    A = _csr_matrix(g)
+    deg = np.asarray(A.sum(axis=1)).ravel()
+    inv = np.where(deg > 0, 1.0 / np.where(deg > 0, deg, 1.0), 0.0)
+    d, n = 0.85, g.n
+    r = np.full(n, 1.0 / n)
+    AT = A.T.tocsr()
+    for _ in range(30):
+        r = (1 - d) / n + d * (AT @ (inv * r))
+    got, st = oracle.pagerank(g.n, g.row_ptr, g.col, T=30, damping=d)
+    np.testing.assert_allclose(got, r, rtol=1e-12, atol=0)
+    assert (deg == 0).any() and A.diagonal().any()
+    assert st["supersteps"] == 31 and st["messages"].tolist() == [g.m] * 30 + [0]
