@@ -297,8 +297,11 @@ int ip_mlp_pack(const float* params, const float* mu_sd, void* blob, void* strea
  *   csr_offsets / csr_cols   the out-edge CSR, DEVICE memory, not modified.
  *   labels         n_vertices uint32 outputs, DEVICE memory.
  *   supersteps_out host pointer or NULL: supersteps run, superstep 0 included.
- * Returns IP_OK at global halt, IP_E_MAXSTEPS at the cap. The input is not
- * validated. The first call on a device looks up the array's device address;
+ * Returns IP_OK at global halt, IP_E_MAXSTEPS at the cap. The input is checked
+ * on the device: offsets that do not start at 0, decrease, or do not end at
+ * n_edges give IP_E_INVAL before any edge is read; an edge whose destination is
+ * not below n_vertices is skipped and the call returns IP_E_RANGE (labels are
+ * then unspecified). The first call on a device looks up the array's device address;
  * make that first call before any stream capture. All calls on a device share
  * the array: calls that overlap on the GPU race and give wrong results. */
 #define IP_NOALLOC_MAX_VERTICES (1u << 20)

@@ -17,6 +17,12 @@
 // same array and leaves its contents behind; each call clears what it needs
 // before use. Calls whose work overlaps on the GPU (two streams, two threads)
 // race on the array and give wrong results.
+//
+// The input is checked on the device before and while it is used: offsets that
+// do not start at 0, decrease, or do not end at n_edges stop the call before any
+// edge is read (IP_E_INVAL); an edge whose destination is not below n_vertices is
+// skipped and recorded (IP_E_RANGE). No access ever leaves the caller's arrays or
+// the scratch array.
 #include <mutex>
 
 #include "internal.h"
@@ -33,15 +39,19 @@ constexpr int NA_BLOCK = 256;
 //   [MAX_V, MAX_V + W)              recipient bitmap of the superstep being computed
 //   [.. + W, .. + 2W)               broadcast bitmap, even supersteps
 //   [.. + 2W, .. + 3W)              broadcast bitmap, odd supersteps
-//   [.. + 3W, .. + 3W + 4)          counters: messages sent (64-bit), spare
+//   [.. + 3W, .. + 3W + 4)          counters: messages sent (64-bit), input error bits, spare
 constexpr size_t NA_WORDS = (size_t)NA_MAX_V + 3 * (size_t)NA_MAX_W + 4;
 static __device__ __align__(256) uint32_t na_scratch[NA_WORDS];
+
+constexpr uint32_t NA_ERR_OFFSETS = 1u;  // offsets[0] != 0, a decreasing offset, or offsets[n] != n_edges
+constexpr uint32_t NA_ERR_IDS = 2u;      // an edge destination >= n_vertices
 
 struct NaPtrs {
     uint32_t* mbox;
     uint32_t* recv;
     uint32_t* bc[2];
     unsigned long long* msgs;
+    uint32_t* err;  // right after msgs: one 16-byte read returns both
 };
 
 NaPtrs na_layout(uint32_t* base) {
@@ -51,7 +61,19 @@ NaPtrs na_layout(uint32_t* base) {
     p.bc[0] = p.recv + NA_MAX_W;
     p.bc[1] = p.bc[0] + NA_MAX_W;
     p.msgs = reinterpret_cast<unsigned long long*>(p.bc[1] + NA_MAX_W);
+    p.err = p.bc[1] + NA_MAX_W + 2;
     return p;
+}
+
+// Offsets check (the err word was zeroed by the host just before): every offset
+// pair non-decreasing, the first 0 and the last n_edges, so every later edge
+// index lies in [0, n_edges).
+__global__ void na_validate(uint32_t n, const uint32_t* off, unsigned long long E, NaPtrs p) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    bool bad = false;
+    for (uint32_t v = tid; v < n; v += nth) bad |= off[v + 1] < off[v];
+    if (tid == 0) bad |= off[0] != 0u || (unsigned long long)off[n] != E;
+    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31u) == 0) atomicOr(p.err, NA_ERR_OFFSETS);
 }
 
 // Superstep 0 (Fig. 9): label = id, every vertex broadcasts. Clears the
@@ -73,23 +95,54 @@ __global__ void na_init(uint32_t n, uint32_t* label, NaPtrs p, unsigned long lon
 
 // Exchange into superstep s: every broadcaster of s-1 pushes its label along
 // its out-edges (min combiner); the bitmap of s is cleared for the apply.
+// A warp takes 32 consecutive vertices: a broadcaster with at most NA_LANE_DEG
+// out-edges is pushed by its own lane, a larger one by the whole warp (one
+// vertex at a time, lanes on consecutive edges), so a hub does not hold up the
+// other lanes of its warp. Destinations >= n are skipped and recorded.
+constexpr uint32_t NA_LANE_DEG = 8;
+__device__ __forceinline__ void na_deliver(uint32_t n, uint32_t v, uint32_t m, const NaPtrs& p, bool& bad) {
+    if (v >= n) {
+        bad = true;
+        return;
+    }
+    atomicMin(p.mbox + v, m);
+    atomicOr(p.recv + (v >> 5), 1u << (v & 31u));
+}
+
 __global__ void na_push(uint32_t n, const uint32_t* off, const uint32_t* col, const uint32_t* label, NaPtrs p,
                         uint32_t s) {
+    if (*(volatile uint32_t*)p.err) return;  // the host stops before this; kept as a guard
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     const uint32_t W = (n + 31) / 32;
     const uint32_t* prev = (s & 1) ? p.bc[0] : p.bc[1];
     uint32_t* next = (s & 1) ? p.bc[1] : p.bc[0];
     for (uint32_t w = tid; w < W; w += nth) next[w] = 0;
     if (tid == 0) *p.msgs = 0;
-    for (uint32_t u = tid; u < n; u += nth) {
-        if (!((prev[u >> 5] >> (u & 31u)) & 1u)) continue;
-        const uint32_t m = label[u];
-        for (uint32_t k = off[u]; k < off[u + 1]; ++k) {
-            const uint32_t v = col[k];
-            atomicMin(p.mbox + v, m);
-            atomicOr(p.recv + (v >> 5), 1u << (v & 31u));
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = nth >> 5;
+    bool bad = false;
+    for (uint32_t w = tid >> 5; w < W; w += warps) {  // warp-uniform loop over 32-vertex words
+        const uint32_t u = w * 32 + lane;
+        const bool b = u < n && ((prev[w] >> lane) & 1u);
+        uint32_t k0 = 0, k1 = 0, m = 0;
+        if (b) {
+            k0 = off[u];
+            k1 = off[u + 1];
+            m = label[u];
+        }
+        const bool big = b && k1 - k0 > NA_LANE_DEG;
+        if (b && !big)
+            for (uint32_t k = k0; k < k1; ++k) na_deliver(n, col[k], m, p, bad);
+        uint32_t todo = __ballot_sync(0xFFFFFFFFu, big);
+        while (todo) {
+            const uint32_t src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t a = __shfl_sync(0xFFFFFFFFu, k0, src), e = __shfl_sync(0xFFFFFFFFu, k1, src);
+            const uint32_t mm = __shfl_sync(0xFFFFFFFFu, m, src);
+            for (uint32_t k = a + lane; k < e; k += 32) na_deliver(n, col[k], mm, p, bad);
         }
     }
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(p.err, NA_ERR_IDS);
 }
 
 // compute() of Fig. 9 for the recipients of superstep s; counts the messages
@@ -157,8 +210,24 @@ extern "C" int ip_hashmin_noalloc(uint32_t n_vertices, uint64_t n_edges, const u
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = sms > 0 ? sms * 4 : 128;
+    // {messages sent (64-bit), error bits}, read back after every superstep
+    struct {
+        unsigned long long sent;
+        uint32_t err, spare;
+    } ctr = {0, 0, 0};
+    auto read_counters = [&]() -> int {
+        if (cudaMemcpyAsync(&ctr, p.msgs, sizeof(ctr), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return IP_E_CUDA;
+        if (ctr.err & NA_ERR_OFFSETS) return IP_E_INVAL;
+        if (ctr.err & NA_ERR_IDS) return IP_E_RANGE;
+        return IP_OK;
+    };
+    if (cudaMemsetAsync(p.err, 0, sizeof(uint32_t), st) != cudaSuccess) return IP_E_CUDA;
+    na_validate<<<grid, NA_BLOCK, 0, st>>>(n_vertices, csr_offsets, (unsigned long long)n_edges, p);
     na_init<<<grid, NA_BLOCK, 0, st>>>(n_vertices, labels, p, (unsigned long long)n_edges);
     if (cudaGetLastError() != cudaSuccess) return IP_E_CUDA;
+    if ((r = read_counters()) != IP_OK) return r;  // bad offsets: no edge has been read
     uint32_t s = 0;  // last completed superstep
     int halted = n_edges == 0;
     while (!halted && s + 1 < max_supersteps) {
@@ -167,11 +236,8 @@ extern "C" int ip_hashmin_noalloc(uint32_t n_vertices, uint64_t n_edges, const u
         na_apply<<<grid, NA_BLOCK, 0, st>>>(n_vertices, csr_offsets, labels, p, s);
         na_clear_recv<<<grid, NA_BLOCK, 0, st>>>(n_vertices, p);
         if (cudaGetLastError() != cudaSuccess) return IP_E_CUDA;
-        unsigned long long sent = 0;
-        if (cudaMemcpyAsync(&sent, p.msgs, sizeof(sent), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return IP_E_CUDA;
-        halted = sent == 0;
+        if ((r = read_counters()) != IP_OK) return r;
+        halted = ctr.sent == 0;
     }
     if (supersteps_out) *supersteps_out = s + 1;
     return halted ? IP_OK : IP_E_MAXSTEPS;

@@ -43,3 +43,29 @@ def test_noalloc_rejects_oversized_graph():
     out = torch.zeros(4, dtype=torch.int32, device="cuda")
     code, _ = ipg.hashmin_noalloc(ipg.NOALLOC_MAX_VERTICES + 1, off, off, out)
     assert code == ipg.IP_E_RANGE
+
+
+def test_noalloc_checks_its_input_then_runs_clean():
+    """Malformed graphs are refused by the entry point's own device checks (no
+    access leaves the arrays), and a valid call right after still matches ip_run."""
+    g = inputs.rmat_graph(10, symmetrize=True, seed=5)
+    out = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    bad_col = g.col.copy()
+    bad_col[len(bad_col) // 2] = g.n + 7  # a destination beyond the last vertex
+    code, _ = ipg.hashmin_noalloc(g.n, _dev(g.row_ptr), _dev(bad_col), out)
+    assert code == ipg.IP_E_RANGE
+    bad_off = g.row_ptr.copy()
+    assert bad_off[3] > 0
+    bad_off[4] = bad_off[3] - 1  # a decreasing pair of offsets
+    code, _ = ipg.hashmin_noalloc(g.n, _dev(bad_off), _dev(g.col), out)
+    assert code == ipg.IP_E_INVAL
+    short = g.row_ptr.copy()
+    short[-1] -= 1  # the last offset is not n_edges
+    code, _ = ipg.hashmin_noalloc(g.n, _dev(short), _dev(g.col), out)
+    assert code == ipg.IP_E_INVAL
+    with ipg.Graph.from_inputs(g) as G:
+        st = G.run("hashmin", policy="threshold")
+        want = G.values("hashmin")
+    code, steps = ipg.hashmin_noalloc(g.n, _dev(g.row_ptr), _dev(g.col), out)
+    assert code == ipg.IP_OK and steps == st.supersteps
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), want)
