@@ -12,6 +12,10 @@ leg, and by nothing else. The GPU product path never imports this package.
 * ``pagerank_update`` — compute() of Fig. 8 for chosen vertices in one superstep,
   from the ranks of the superstep before (FP64 numpy): checks a single superstep
   of a run too large for the full oracle, one vertex at a time.
+  ``pagerank_superstep`` is the same update for a range of vertices in C, used
+  to check and to time one superstep of a billion-edge graph.
+* PageRank to convergence (``pagerank(..., tolerance=eps)``): the run ends after
+  the first superstep whose L1 rank change is below eps.
 * ``mlp.py`` — FP64 forward/backward of the 8-32-32-3 mode-selector MLP.
 
 The compiled part is built on first use with gcc (``build()``).
@@ -39,7 +43,7 @@ F64 = ctypes.POINTER(ctypes.c_double)
 
 class _Stats(ctypes.Structure):
     _fields_ = [("supersteps", ctypes.c_uint32), ("halted", ctypes.c_int32), ("cap", ctypes.c_uint32),
-                ("active", U32), ("broadcasters", U32), ("messages", U64)]
+                ("active", U32), ("broadcasters", U32), ("messages", U64), ("delta", F64)]
 
 
 def build(force: bool = False) -> str:
@@ -47,7 +51,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp], check=True,
+    subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"], check=True,
                    capture_output=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -61,7 +65,10 @@ def _L():
             lib = ctypes.CDLL(_LIB_PATH)
             st = ctypes.POINTER(_Stats)
             lib.oracle_pagerank.argtypes = [ctypes.c_uint32, U32, U32, ctypes.c_uint32, ctypes.c_double,
-                                            ctypes.c_uint32, F64, st]
+                                            ctypes.c_double, ctypes.c_uint32, F64, st]
+            lib.oracle_pagerank_superstep.argtypes = [ctypes.c_uint32, U32, U32, U32, F64, ctypes.c_double,
+                                                      ctypes.c_uint32, ctypes.c_uint32, F64]
+            lib.oracle_pagerank_superstep.restype = None
             lib.oracle_hashmin.argtypes = [ctypes.c_uint32, U32, U32, ctypes.c_uint32, U32, st]
             lib.oracle_sssp.argtypes = [ctypes.c_uint32, U32, U32, U32, ctypes.c_uint32, ctypes.c_uint32, U32, st]
             for f in (lib.oracle_pagerank, lib.oracle_hashmin, lib.oracle_sssp):
@@ -81,29 +88,53 @@ def _stats(cap):
     act = np.zeros(max(cap, 1), np.uint32)
     bc = np.zeros(max(cap, 1), np.uint32)
     msg = np.zeros(max(cap, 1), np.uint64)
-    s = _Stats(0, 0, cap, act.ctypes.data_as(U32), bc.ctypes.data_as(U32), msg.ctypes.data_as(U64))
-    return s, (act, bc, msg)
+    dl = np.zeros(max(cap, 1), np.float64)
+    s = _Stats(0, 0, cap, act.ctypes.data_as(U32), bc.ctypes.data_as(U32), msg.ctypes.data_as(U64),
+               dl.ctypes.data_as(F64))
+    return s, (act, bc, msg, dl)
 
 
 def _finish(r, s, arrs):
     if r < 0:
         raise MemoryError("oracle allocation failed")
     n = min(s.supersteps, s.cap)
-    act, bc, msg = arrs
+    act, bc, msg, dl = arrs
     return dict(supersteps=int(s.supersteps), halted=bool(s.halted), active=act[:n].copy(),
-                broadcasters=bc[:n].copy(), messages=msg[:n].copy())
+                broadcasters=bc[:n].copy(), messages=msg[:n].copy(), delta=dl[:n].copy())
 
 
-def pagerank(n, row_ptr, col, T=30, damping=0.85, max_supersteps=None, stats_cap=None):
-    """FP64 synchronous-Pregel PageRank (Fig. 8). Returns (rank[n] float64, stats)."""
+def pagerank(n, row_ptr, col, T=30, damping=0.85, max_supersteps=None, stats_cap=None, tolerance=0.0):
+    """FP64 synchronous-Pregel PageRank (Fig. 8). Returns (rank[n] float64, stats).
+
+    tolerance > 0: PageRank to convergence — the run also ends after the first
+    superstep s >= 1 whose L1 change sum_v |r_s(v) - r_(s-1)(v)| (stats["delta"][s])
+    is below tolerance; T still bounds the run."""
     if max_supersteps is None:
         max_supersteps = T + 1
     cap = max_supersteps if stats_cap is None else stats_cap
     out = np.zeros(max(n, 1), np.float64)
     s, arrs = _stats(cap)
     r = _L().oracle_pagerank(n, _u32(row_ptr).ctypes.data_as(U32), _u32(col).ctypes.data_as(U32), T,
-                             float(damping), max_supersteps, out.ctypes.data_as(F64), ctypes.byref(s))
+                             float(damping), float(tolerance), max_supersteps, out.ctypes.data_as(F64),
+                             ctypes.byref(s))
     return out[:n], _finish(r, s, arrs)
+
+
+def pagerank_superstep(n, in_ptr, in_src, out_degree, prev_rank, damping=0.85, v_begin=0, v_end=None):
+    """One superstep s >= 1 of PageRank (Fig. 8) for the vertices [v_begin, v_end),
+    in C (pregel.c, oracle_pagerank_superstep): the same definition as
+    pagerank_update, fast enough to check or time a billion-edge superstep.
+    in_ptr/in_src: in-edge arrays (uint32); out_degree: uint32; prev_rank: float64.
+    Returns rank[v_end - v_begin] float64."""
+    v_end = n if v_end is None else v_end
+    ip, isrc = _u32(in_ptr), _u32(in_src)
+    od = _u32(out_degree)
+    prev = np.ascontiguousarray(prev_rank, dtype=np.float64)
+    out = np.empty(max(v_end - v_begin, 1), np.float64)
+    _L().oracle_pagerank_superstep(n, ip.ctypes.data_as(U32), isrc.ctypes.data_as(U32), od.ctypes.data_as(U32),
+                                   prev.ctypes.data_as(F64), float(damping), int(v_begin), int(v_end),
+                                   out.ctypes.data_as(F64))
+    return out[:v_end - v_begin]
 
 
 def hashmin(n, row_ptr, col, max_supersteps=1 << 30, stats_cap=4096):

@@ -35,6 +35,7 @@
  * A vertex with out-degree 0 broadcasts to nobody, so PageRank mass at
  * dangling vertices is dropped, as in the Pregel version (Fig. 12).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -48,6 +49,8 @@ typedef struct {
     uint32_t* active;    /* per superstep: vertices that ran compute() */
     uint32_t* broadcasters; /* per superstep: vertices that called broadcast() */
     uint64_t* messages;  /* per superstep: messages sent */
+    double* delta;       /* per superstep (PageRank, may be NULL): sum over vertices of
+                            |rank after the superstep - rank before it| (0 for superstep 0) */
 } oracle_stats;
 
 /* ------------------------------------------------------------------ graph */
@@ -88,6 +91,10 @@ struct engine {
     double damping;
     uint32_t T;
     uint32_t source;
+    /* PageRank to convergence: the run ends after the first superstep s >= 1 whose
+     * L1 change (delta) is below tolerance; 0 disables the test */
+    double tolerance;
+    double delta;
 };
 
 /* Fig. 5: the min combiner. */
@@ -162,7 +169,9 @@ static void compute_pagerank(engine* e, vertex* me) {
     } else {
         double sum = 0.0, msg;
         while (get_next_message_f(e, me, &msg)) sum += msg;
+        const double old_value = me->value_f;
         me->value_f = (1.0 - e->damping) / N + e->damping * sum;
+        e->delta += fabs(me->value_f - old_value);
     }
     if (get_superstep(e) < e->T) {
         if (me->out_neighbour_count > 0)
@@ -216,6 +225,7 @@ static int run(engine* e, compute_fn compute, uint32_t max_supersteps, oracle_st
         e->superstep = s;
         e->broadcasters = 0;
         e->messages = 0;
+        e->delta = 0.0;
         uint32_t active = 0;
         memset(e->consumed, 0, n);
         for (uint32_t v = 0; v < n; ++v) {
@@ -230,6 +240,15 @@ static int run(engine* e, compute_fn compute, uint32_t max_supersteps, oracle_st
             st->active[s] = active;
             st->broadcasters[s] = e->broadcasters;
             st->messages[s] = e->messages;
+            if (st->delta) st->delta[s] = e->delta;
+        }
+        /* convergence (PageRank with a tolerance): after the global synchronisation
+         * of superstep s >= 1 the run ends when the ranks moved by less than the
+         * tolerance in total; the broadcasts of s are never read */
+        if (e->tolerance > 0.0 && s >= 1 && e->delta < e->tolerance) {
+            halted_globally = 1;
+            ++s;
+            break;
         }
         /* global synchronisation: messages sent in s become readable in s+1 */
         uint8_t* th = e->has_msg[0];
@@ -302,11 +321,12 @@ static void teardown(engine* e) {
 /* Public entry points. Return 1 on global halt, 0 when the cap stopped the
  * run, -1 on allocation failure. */
 int oracle_pagerank(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, uint32_t T, double damping,
-                    uint32_t max_supersteps, double* value_out, oracle_stats* st) {
+                    double tolerance, uint32_t max_supersteps, double* value_out, oracle_stats* st) {
     engine e;
     if (setup(&e, n, row_ptr, col, NULL, 1)) return -1;
     e.T = T;
     e.damping = damping;
+    e.tolerance = tolerance;
     int r = run(&e, compute_pagerank, max_supersteps, st);
     for (uint32_t v = 0; v < n; ++v) value_out[v] = e.vertices[v].value_f;
     teardown(&e);
@@ -332,4 +352,26 @@ int oracle_sssp(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, const 
     for (uint32_t v = 0; v < n; ++v) value_out[v] = e.vertices[v].value;
     teardown(&e);
     return r;
+}
+
+/* One superstep s >= 1 of PageRank (Fig. 8 with the constant of Fig. 12) for the
+ * vertices [v_begin, v_end), written from the receiving side: in superstep s-1
+ * every in-neighbour u of v broadcast prev_rank[u] / out_degree[u] (u has at
+ * least one out-edge, the one to v), the sum combiner added those messages, and
+ * compute() takes (1-d)/N + d * sum. in_ptr / in_src are the in-edge arrays.
+ * out[v - v_begin] receives the new rank. Independent vertices: any split of the
+ * range gives the same values. Used to check one superstep of a graph too large
+ * for a whole oracle run, and to time bounded samples of a run. */
+void oracle_pagerank_superstep(uint32_t n, const uint32_t* in_ptr, const uint32_t* in_src,
+                               const uint32_t* out_degree, const double* prev_rank, double damping,
+                               uint32_t v_begin, uint32_t v_end, double* out) {
+    const double base = (1.0 - damping) / (double)n;
+    for (uint32_t v = v_begin; v < v_end; ++v) {
+        double sum = 0.0;
+        for (uint32_t k = in_ptr[v]; k < in_ptr[v + 1]; ++k) {
+            const uint32_t u = in_src[k];
+            sum += prev_rank[u] / (double)out_degree[u];
+        }
+        out[v - v_begin] = base + damping * sum;
+    }
 }

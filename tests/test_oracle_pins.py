@@ -360,3 +360,102 @@ def test_pagerank_sparse_power_iteration(scale):
     np.testing.assert_allclose(got, r, rtol=1e-12, atol=0)
     assert (deg == 0).any() and A.diagonal().any()
     assert st["supersteps"] == 31 and st["messages"].tolist() == [g.m] * 30 + [0]
+
+
+# ------------------------------------------------- PageRank, one superstep in C
+def test_pagerank_superstep_exact_fractions():
+    """The C one-superstep update (pull form) against exact rationals, any split of
+    the vertex range giving the same values."""
+    edges = [(0, 1), (0, 2), (1, 2), (2, 0), (2, 3), (4, 2), (3, 3)]
+    n, d = 5, Fraction(85, 100)
+    g = inputs.from_edges(n, [a for a, _ in edges], [b for _, b in edges])
+    outd = [sum(1 for a, _ in edges if a == v) for v in range(n)]
+    prev = [Fraction(k + 1, 17) for k in range(n)]
+    want = [(1 - d) / n] * n
+    for a, b in edges:
+        want[b] += d * prev[a] / outd[a]
+    pf = [float(x) for x in prev]
+    got = oracle.pagerank_superstep(n, g.t_ptr, g.t_idx, g.out_degree(), pf)
+    np.testing.assert_allclose(got, [float(x) for x in want], rtol=1e-15)
+    parts = np.concatenate([oracle.pagerank_superstep(n, g.t_ptr, g.t_idx, g.out_degree(), pf, v_begin=a, v_end=b)
+                            for a, b in ((0, 2), (2, 2), (2, 5))])
+    assert np.array_equal(parts, got)
+
+
+def test_pagerank_superstep_continues_the_engine():
+    """From the ranks of a T - 1 run of the push-based engine, one pull-form superstep
+    gives the T run (R-MAT with hubs, self-loops and dangling vertices)."""
+    g = inputs.rmat_graph(11, seed=9)
+    r9, _ = oracle.pagerank(g.n, g.row_ptr, g.col, T=9)
+    r10, _ = oracle.pagerank(g.n, g.row_ptr, g.col, T=10)
+    got = oracle.pagerank_superstep(g.n, g.t_ptr, g.t_idx, g.out_degree(), r9)
+    np.testing.assert_allclose(got, r10, rtol=1e-13)
+    assert (g.out_degree() == 0).any()
+
+
+# ------------------------------------------------- PageRank to convergence
+def _star_iterates(k, T, d=0.85):
+    """Closed form of the symmetric star's iterates t = 0..T (centre, leaf)."""
+    N = k + 1
+    rc = (1 + d * k) / (N * (1 + d))
+    rl = (1 - d) / N + d * rc / k
+    ec, el = 1.0 / N - rc, 1.0 / N - rl
+    out = [(rc + ec, rl + el)]
+    for _ in range(T):
+        ec, el = d * k * el, d * ec / k
+        out.append((rc + ec, rl + el))
+    return out
+
+
+@pytest.mark.parametrize("k", [5, 40])
+def test_pagerank_convergence_star_closed_form(k):
+    """Star: the L1 change of superstep t is |c_t - c_(t-1)| + k |l_t - l_(t-1)| from
+    the closed-form iterates, so the halting superstep for a tolerance eps is the
+    first t >= 1 with that change below eps, and the ranks are the iterate t."""
+    its = _star_iterates(k, 200)
+    delta = [0.0] + [abs(its[t][0] - its[t - 1][0]) + k * abs(its[t][1] - its[t - 1][1]) for t in range(1, 201)]
+    g = inputs.star(k)
+    for eps in (1e-3, 1e-6, 1e-9):
+        t_halt = next(t for t in range(1, 201) if delta[t] < eps)
+        r, st = oracle.pagerank(g.n, g.row_ptr, g.col, T=200, tolerance=eps)
+        assert st["halted"] and st["supersteps"] == t_halt + 1, (eps, st["supersteps"], t_halt)
+        np.testing.assert_allclose(st["delta"][1:], delta[1:t_halt + 1], rtol=1e-9, atol=1e-14)
+        np.testing.assert_allclose(r[0], its[t_halt][0], rtol=1e-13)
+        np.testing.assert_allclose(r[1:], its[t_halt][1], rtol=1e-13)
+
+
+def test_pagerank_convergence_cycle_halts_at_once():
+    """Directed cycle: every iterate is 1/N, so the first update changes nothing and
+    the run halts after superstep 1."""
+    g = inputs.directed_cycle(9)
+    r, st = oracle.pagerank(g.n, g.row_ptr, g.col, T=30, tolerance=1e-12)
+    assert st["halted"] and st["supersteps"] == 2 and st["delta"][1] == 0.0
+    np.testing.assert_allclose(r, 1.0 / 9, rtol=1e-15)
+
+
+def test_pagerank_convergence_matches_dense_iteration():
+    """A graph with dangling vertices and self-loops: the oracle's per-superstep L1
+    change equals the dense matrix iteration's, and with the tolerance between two
+    of them the run stops at the first superstep below it; T still caps the run."""
+    g = inputs.rmat_graph(8, seed=3)
+    A = np.zeros((g.n, g.n))
+    s, t = g.edges()
+    A[s, t] = 1.0
+    deg = A.sum(axis=1)
+    inv = np.where(deg > 0, 1.0 / np.where(deg > 0, deg, 1), 0.0)
+    d, n = 0.85, g.n
+    r = [np.full(n, 1.0 / n)]
+    for _ in range(40):
+        r.append((1 - d) / n + d * (A.T @ (inv * r[-1])))
+    delta = [0.0] + [float(np.abs(r[i] - r[i - 1]).sum()) for i in range(1, 41)]
+    _, st = oracle.pagerank(g.n, g.row_ptr, g.col, T=40)
+    np.testing.assert_allclose(st["delta"][1:], delta[1:], rtol=1e-9)
+    t_halt = 12
+    eps = float(np.sqrt(delta[t_halt] * delta[t_halt - 1]))  # between supersteps 11 and 12
+    assert delta[t_halt] < eps < delta[t_halt - 1]
+    got, st = oracle.pagerank(g.n, g.row_ptr, g.col, T=40, tolerance=eps)
+    assert st["halted"] and st["supersteps"] == t_halt + 1
+    np.testing.assert_allclose(got, r[t_halt], rtol=1e-12)
+    got, st = oracle.pagerank(g.n, g.row_ptr, g.col, T=5, tolerance=eps)  # the cap T comes first
+    assert st["halted"] and st["supersteps"] == 6
+    np.testing.assert_allclose(got, r[5], rtol=1e-12)
