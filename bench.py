@@ -1,18 +1,26 @@
 #!/usr/bin/env python3
 """Benchmark of the synchronous vertex-centric superstep library on one GB300.
 
-Workload (one "step"): Hashmin connected components and SSSP from vertex 0 on
-the symmetrised R-MAT graph of scale 22 (4,194,304 vertices, edge factor 16,
-(a,b,c,d) = (.57,.19,.19,.05), seed 1, duplicates removed, uint32 weights
-uniform in [1, 255]), each run to global halt with the default mode policy.
+Default workload (one "step"): the billion-edge configuration — directed R-MAT
+scale 26 (67,108,864 vertices, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05),
+seed 1, duplicates removed: 1,060,392,804 edges), PageRank with T = 30 rank
+updates in pull (blocked pull engine), plus Hashmin connected components on the
+symmetrised form of the same edges (2,103,866,764 directed edges), each run to
+global halt.
 
-Metric: GTEPS = messages sent (sum over supersteps of the out-degrees of the
-broadcasting vertices, both apps) / step time. The JSON line also carries the
-roofline of the dominant kernel (algorithmic bytes / CUDA-event time against
-the measured HBM copy bandwidth), the end-to-end number through the C ABI with
-host buffers, and the CPU oracle timed on the host cores.
+Metric: GTEPS = edges traversed by messages (PageRank: E per broadcasting
+superstep, T·E per run; Hashmin: the out-degrees of the broadcasting vertices,
+summed over supersteps) / step time. The JSON line also carries the roofline of
+the dominant kernel (the blocked pull's two launches per superstep: 8E + 20V
+algorithmic bytes over their CUDA-event time, against the measured HBM copy
+bandwidth), the end-to-end number through the C ABI from pinned host buffers,
+the device memory footprint, and the CPU oracle timed on the host cores. The
+secondary configurations (Hashmin + SSSP on symmetrised R-MAT 22, PageRank on
+R-MAT 16) are reported under per_app.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+  python bench.py --config c2|c1|c4        secondary configurations, one line each
+  python bench.py --ncu-case APP:MODE[:ENGINE] --scale S   small profiling case
 """
 from __future__ import annotations
 
@@ -29,31 +37,45 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-SCALE = 22
+SCALE = 26
 EDGE_FACTOR = 16
+T_PR = 30
+C2_SCALE = 22
 METRIC = "GTEPS & % HBM BW per app (PageRank/Hashmin/SSSP); learned vs fixed push/pull"
-WORKLOAD = ("Hashmin + SSSP(source 0) on symmetrised R-MAT scale 22, edge factor 16, "
-            "(a,b,c,d)=(.57,.19,.19,.05), seed 1, duplicates removed, uint32 weights in [1,255]")
+WORKLOAD = ("billion-edge: PageRank T=30 pull on directed R-MAT scale 26 (edge factor 16, "
+            "(a,b,c,d)=(.57,.19,.19,.05), seed 1, duplicates removed) + Hashmin on its symmetrised form")
+C2_WORKLOAD = ("Hashmin + SSSP(source 0) on symmetrised R-MAT scale 22, edge factor 16, "
+               "(a,b,c,d)=(.57,.19,.19,.05), seed 1, duplicates removed, uint32 weights in [1,255]")
 L2_BYTES = 129 * 1024 * 1024
 
 
-def build_graph(scale=SCALE):
+def c2_graph(scale=C2_SCALE):
     import inputs
     return inputs.rmat_graph(scale, edge_factor=EDGE_FACTOR, a=0.57, b=0.19, c=0.19, seed=1, symmetrize=True,
                              weighted=True, wseed=1)
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum) of a
-    kernel on the workload it is reported for, from profiles/traffic.json (written
-    from an ncu capture of the same command; None when not captured)."""
+def c5_graphs(scale=SCALE, symmetric=True):
+    """The directed R-MAT graph (with its host CSC) and, if asked, its symmetrised form."""
+    import inputs
+    src, dst = inputs.rmat_edges(scale, EDGE_FACTOR << scale, 0.57, 0.19, 0.19, 1)
+    d = inputs.from_edges(1 << scale, src, dst)
+    s = inputs.from_edges(1 << scale, src, dst, symmetrize=True) if symmetric else None
+    return d, s
+
+
+def stored_traffic(kernel):
+    """DRAM bytes per launch of a kernel from profiles/traffic.json: an ncu capture
+    (dram__bytes_read.sum + dram__bytes_write.sum) on a small case, scaled to the
+    benchmark's workload by the edges processed. A stored profile figure, not a
+    measurement of this run; None when the kernel has no capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel)
-    return None if e is None else e.get("bytes_per_launch")
+    return None if e is None else e.get("bytes_per_launch_at_benchmark_size")
 
 
 def measured_peaks():
@@ -63,6 +85,13 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 # ----------------------------------------------------------------- clocks
@@ -158,40 +187,44 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- kernel byte models
-def launches_of(mode_seq, app):
+def launches_of(mode_seq, app, blocked=False):
     """Kernels one run launches: init + selector, then per superstep the mode's kernels + selector."""
     n = 2
     for m in mode_seq[1:]:
         if app == "pagerank":
-            n += 2 if m == 2 else 3
+            n += (3 if blocked else 2) if m == 2 else 3
         else:
             n += 4 if m == 0 else 3
     return n
 
 
-def exchange_bytes(app, mode, V, E, msgs_prev, bcast_prev, recipients):
-    """Algorithmic bytes of one exchange launch delivering the broadcasts of the previous superstep.
+def pr_pull_bytes(V, E):
+    """Algorithmic bytes of one PageRank pull superstep: 4E in-edge indices + 4E
+    gathered source broadcasts + 20V (offsets, rank write, broadcast write,
+    out-degree, sum) = 8E + 20V."""
+    return 8 * E + 20 * V
 
-    pull:        4(V+1) offsets + 4E in-edge sources + V/8 broadcast bitmap + 4 per gathered
-                 broadcast value (msgs_prev) [+ 4 per gathered weight, SSSP] + 4 per recipient mailbox
-    push:        per sender 8 (offsets) + 4 (value) [+ 4 queue entry, sparse]; per message 4 (target)
-                 [+ 4 weight, SSSP] + 4 (mailbox combine); bitmap V/8 (dense)
-    PageRank pull (fused with apply): 4(V+1) + 4E + 4E gathers + 16V (inv out-degree, rank, next value)."""
+
+def exchange_bytes(app, mode, V, E, active_sources, bcast_prev, recipients, weighted_edges=0):
+    """Algorithmic bytes of one min-app exchange launch delivering the broadcasts of
+    the previous superstep.
+
+    pull:  4E in-edge sources (+ 4E in-edge weights, SSSP) + 4 per gathered active
+           source + 16V (offsets, mailbox, broadcast slot, recipient and broadcast bits)
+    push:  16 per sender (offsets, value, queue entry or bitmap word) + per message
+           (8 Hashmin / 12 SSSP: target, weight, the combining RMW counted once) + 20 per
+           recipient."""
     w = 4 if app == "sssp" else 0
-    if app == "pagerank":
-        if mode == 2:
-            return 4 * (V + 1) + 8 * E + 16 * V
-        return 4 * (V + 1) + 8 * E + 4 * V  # push: offsets, targets, atomic adds, values
     if mode == 2:
-        return 4 * (V + 1) + 4 * E + V / 8 + (4 + w) * msgs_prev + 4 * recipients
-    per_sender = 12 + (4 if mode == 0 else 0)
-    return per_sender * bcast_prev + (8 + w) * msgs_prev + (V / 8 if mode == 1 else 0)
+        return 4 * E + w * E + 4 * active_sources + 16 * V
+    per_msg = 8 + w
+    return 16 * bcast_prev + per_msg * active_sources + 20 * recipients
 
 
 KERNEL_NAMES = {("pull", "hashmin"): "k_pull<Hashmin>", ("pull", "sssp"): "k_pull<SSSP>",
                 ("push_dense", "hashmin"): "k_push<Hashmin,dense>", ("push_dense", "sssp"): "k_push<SSSP,dense>",
                 ("push_sparse", "hashmin"): "k_push<Hashmin,sparse>",
-                ("push_sparse", "sssp"): "k_push<SSSP,sparse>", ("pull", "pagerank"): "k_pr_pull"}
+                ("push_sparse", "sssp"): "k_push<SSSP,sparse>"}
 MODE_NAMES = {0: "push_sparse", 1: "push_dense", 2: "pull"}
 
 
@@ -210,7 +243,108 @@ def reduce_over_ranks(total_ms, msgs, world, device=None):
     return float(tmax[0].item()), float(tsum[1].item())
 
 
+# ----------------------------------------------------------------- CPU oracle pool
+# One superstep of PageRank by the oracle (oracle.pagerank_superstep, FP64, plain
+# loops), statically partitioned over the host cores: every worker process takes a
+# contiguous range of vertices (the paper's static OpenMP schedule over vertices),
+# the graph shared through shared memory. The oracle itself is unchanged.
+_W = {}
+
+
+def _pool_attach(spec):
+    from multiprocessing import shared_memory
+    import oracle
+    oracle.build()
+    arrs = {}
+    for name, (shm_name, dtype, count) in spec.items():
+        shm = shared_memory.SharedMemory(name=shm_name)
+        _W.setdefault("shm", []).append(shm)
+        arrs[name] = np.ndarray((count,), dtype=np.dtype(dtype), buffer=shm.buf)
+    _W["a"] = arrs
+
+
+def _pool_task(rng):
+    import oracle
+    a = _W["a"]
+    v0, v1 = rng
+    out = oracle.pagerank_superstep(int(a["n"][0]), a["t_ptr"], a["t_idx"], a["outdeg"], a["prev"], 0.85, v0, v1)
+    a["out"][v0:v1] = out
+    return v1 - v0
+
+
+class OraclePool:
+    """Spawned worker processes (no fork after CUDA use) running the oracle's
+    one-superstep PageRank update on disjoint vertex ranges of one shared graph."""
+
+    def __init__(self, g, workers):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        self.n, self.workers = g.n, workers
+        src = {"n": np.array([g.n], np.uint32), "t_ptr": g.t_ptr, "t_idx": g.t_idx,
+               "outdeg": g.out_degree().astype(np.uint32), "prev": np.full(g.n, 1.0 / g.n),
+               "out": np.zeros(g.n, np.float64)}
+        self.shm, spec = [], {}
+        for name, arr in src.items():
+            arr = np.ascontiguousarray(arr)
+            shm = shared_memory.SharedMemory(create=True, size=max(arr.nbytes, 8))
+            np.ndarray(arr.shape, arr.dtype, buffer=shm.buf)[:] = arr
+            self.shm.append(shm)
+            spec[name] = (shm.name, arr.dtype.str, arr.size)
+        self.in_ptr = g.t_ptr
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_pool_attach, initargs=(spec,))
+        self.pool.map(_pool_task, [(0, 0)] * workers)  # workers up and attached
+
+    def superstep(self, v_begin=0, v_end=None, parts=None):
+        """Seconds for one oracle superstep over [v_begin, v_end), split into `parts`
+        equal vertex ranges (default: one per worker)."""
+        v_end = self.n if v_end is None else v_end
+        parts = self.workers if parts is None else parts
+        cuts = np.linspace(v_begin, v_end, parts + 1).astype(np.int64)
+        t0 = time.perf_counter()
+        self.pool.map(_pool_task, [(int(cuts[i]), int(cuts[i + 1])) for i in range(parts)], chunksize=1)
+        return time.perf_counter() - t0
+
+    def edges(self, v_begin=0, v_end=None):
+        v_end = self.n if v_end is None else v_end
+        return int(self.in_ptr[v_end]) - int(self.in_ptr[v_begin])
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        for s in self.shm:
+            s.close()
+            s.unlink()
+
+
+def cpu_oracle_baseline(pool, g):
+    """The oracle's PageRank superstep on the host: all cores (static vertex ranges,
+    one per core) over the whole graph, and one core over a slice of it."""
+    secs = min(pool.superstep() for _ in range(2))
+    all_cores = {"value": round(g.m / secs / 1e9, 5), "unit": "GTEPS", "cores": pool.workers, "kind": "oracle",
+                 "sample": ("one PageRank superstep (Fig. 8, FP64, oracle.pagerank_superstep) over all "
+                            f"{g.n:,} vertices and {g.m:,} edges of the directed graph, static vertex ranges "
+                            "over every host core; Hashmin not sampled"),
+                 "seconds": round(secs, 3), "host_cores": host_cores()}
+    v1 = int(np.searchsorted(g.t_ptr, g.m // 8))  # about an eighth of the edges
+    t1 = pool.superstep(0, v1, parts=1)
+    all_cores["single_thread"] = {"value": round(pool.edges(0, v1) / t1 / 1e9, 5), "unit": "GTEPS", "cores": 1,
+                                  "sample": f"the same superstep for vertices [0, {v1:,}) ({pool.edges(0, v1):,} edges)",
+                                  "seconds": round(t1, 3)}
+    return all_cores
+
+
 # ----------------------------------------------------------------- GPU arm
+def memory_report(G, name):
+    info = G.info()
+    V, E = info["n_vertices"], info["n_edges"]
+    rep = {"graph": name, "vertices": V, "edges": E, "device_bytes": info["device_bytes"],
+           "bytes_per_vertex": round(info["device_bytes"] / V, 2), "bytes_per_edge": round(info["device_bytes"] / E, 3)}
+    parts = {k[len("bytes_"):]: info[k] for k in info if k.startswith("bytes_") and info[k]}
+    if parts:
+        rep["breakdown"] = parts
+    return rep
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2010_08781_gb300 as ipg
@@ -218,32 +352,34 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
-    g = build_graph(args.scale)
-    V, E = g.n, g.m
-    # pinned host copies of the inputs (for the end-to-end leg)
-    pin = {k: torch.from_numpy(getattr(g, k).view(np.int32)).pin_memory() for k in ("row_ptr", "col", "w")}
+    d, s = c5_graphs(args.scale)
+    V, Ed, Es = d.n, d.m, s.m
+    # the CPU oracle's workers are spawned (not forked) and stay idle until the GPU legs are done
+    pool = OraclePool(d, host_cores()) if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    # pinned host copies of the inputs (the end-to-end leg copies them every step)
+    pin = {k: torch.from_numpy(v.view(np.int32)).pin_memory()
+           for k, v in (("d_ptr", d.row_ptr), ("d_col", d.col), ("s_ptr", s.row_ptr), ("s_col", s.col))}
     with torch.cuda.stream(stream):
-        G = ipg.Graph(V, pin["row_ptr"], pin["col"], pin["w"], symmetric=True, stream=stream)
+        P = ipg.Graph(V, pin["d_ptr"], pin["d_col"], stream=stream)  # in-edges transposed on the device
+        H = ipg.Graph(V, pin["s_ptr"], pin["s_col"], symmetric=True, stream=stream)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    opts = dict(policy=args.policy, stream=stream)
+    pr_kw = dict(policy="forced", forced_mode="pull", pr_iterations=T_PR, stream=stream)
+    hm_kw = dict(policy=args.policy, stream=stream)
 
     def step():
-        a = G.run("hashmin", **opts)
-        b = G.run("sssp", source=0, **opts)
-        return a, b
+        return P.run("pagerank", **pr_kw), H.run("hashmin", **hm_kw)
 
     clk = ClockSampler(local_rank).__enter__()  # sampling from before the warm-up
     for _ in range(args.warmup):
-        step()
+        step()  # the first one also builds the blocked layout
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    msgs = 0
-    launches = 0
-    per_app = {"hashmin": [], "sssp": []}
+    msgs = launches = 0
+    runs = {"pagerank": [], "hashmin": []}
     clk.start()
     try:
         for i in range(args.steps):
@@ -254,9 +390,9 @@ def run_gpu(args, rank, world, local_rank):
             with torch.cuda.stream(stream):
                 ev[i][1].record(stream)
             msgs += int(a.messages.sum()) + int(b.messages.sum())
-            launches += launches_of(a.mode.tolist(), "hashmin") + launches_of(b.mode.tolist(), "sssp")
-            per_app["hashmin"].append(a)
-            per_app["sssp"].append(b)
+            launches += launches_of(a.mode.tolist(), "pagerank", blocked=True) + launches_of(b.mode.tolist(), "hashmin")
+            runs["pagerank"].append(a)
+            runs["hashmin"].append(b)
         torch.cuda.synchronize()
     finally:
         clk.stop()
@@ -266,135 +402,147 @@ def run_gpu(args, rank, world, local_rank):
     value = msgs_all / (total_ms * 1e-3) / 1e9
 
     # ---------------------------------------------------------- roofline of the dominant kernel
+    # Host-driven replay of the timed PageRank runs (same engine, same graph state), CUDA
+    # events on the launching stream around the two blocked-pull launches of every superstep.
     peak, peak_kind = measured_peaks()
-    kern = {}  # name -> [total ms, total bytes, launches]
-    # the timed runs' own mode sequences are replayed (the learned selector reads the
-    # last superstep's time, which events and profilers change)
-    seqs = {app: per_app[app][-1].mode[1:per_app[app][-1].supersteps].tolist() for app in ("hashmin", "sssp")}
-    for _ in range(args.steps):
-        for app in ("hashmin", "sssp"):
-            st = G.run(app, profile_kernels=1, stream=stream, mode_sequence=seqs[app])
-            for s in range(1, st.supersteps):
-                mode = int(st.mode[s])
-                name = KERNEL_NAMES[(MODE_NAMES[mode], app)]
-                by = exchange_bytes(app, mode, V, E, int(st.messages[s - 1]), int(st.broadcasters[s - 1]),
-                                    int(st.active[s]))
-                k = kern.setdefault(name, [0.0, 0.0, 0])
-                k[0] += float(st.kernel_ms[s, 1])
-                k[1] += by
-                k[2] += 1
-                a = kern.setdefault("k_apply_" + ("queue" if mode == 0 else "bitmap"), [0.0, 0.0, 0])
-                a[0] += float(st.kernel_ms[s, 2])
-                a[2] += 1
-    dom = max((n for n in kern if kern[n][1] > 0), key=lambda n: kern[n][0])
-    d_ms, d_bytes, d_n = kern[dom]
-    achieved = d_bytes / (d_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": measured_traffic(dom), "launches_per_step": d_n / args.steps,
-                "avg_launch_us": round(1e3 * d_ms / d_n, 2)}
-    total_k = sum(v[0] for v in kern.values())
-    roofline["share_of_kernel_time"] = round(d_ms / total_k, 3)
+    by = pr_pull_bytes(V, Ed)
+    pull_ms = []
+    for _ in range(min(args.steps, 3)):
+        st = P.run("pagerank", profile_kernels=1, **pr_kw)
+        pull_ms += [float(x) for x in st.kernel_ms[1:st.supersteps, 1]]
+    avg = sum(pull_ms) / len(pull_ms)
+    achieved = by / (avg * 1e-3) / 1e9
+    pr_ms = statistics.median(r.elapsed_ms for r in runs["pagerank"])
+    hm_ms = statistics.median(r.elapsed_ms for r in runs["hashmin"])
+    roofline = {"bound": "hbm", "kernel": "k_pb_scatter+k_pb_accumulate", "achieved": round(achieved, 1),
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": stored_traffic("k_pb_scatter+k_pb_accumulate"),
+                "traffic_note": ("stored ncu figure (profiles/traffic.json: R-MAT 23 capture scaled by edges), "
+                                 "not measured in this run"),
+                "bytes_per_launch": by, "launches_per_step": T_PR, "avg_launch_us": round(1e3 * avg, 2),
+                "timing": "CUDA events per superstep around the pull launches, host-driven replay after the timed region",
+                "timed_region_lower_bound_gbs": round(by * T_PR / (pr_ms * 1e-3) / 1e9, 1),
+                "share_of_step": round(T_PR * avg / (pr_ms + hm_ms), 3)}
+
+    # ---------------------------------------------------------- per app, policies, memory
+    detail = {}
+    pm = int(runs["pagerank"][0].messages.sum())
+    detail["pagerank"] = {"gteps": round(pm / (pr_ms * 1e-3) / 1e9, 2), "ms": round(pr_ms, 3),
+                          "ms_per_iteration": round(pr_ms / T_PR, 4), "supersteps": runs["pagerank"][0].supersteps,
+                          "vertices": V, "edges": Ed, "engine": "blocked"}
+    gather = min(P.run("pagerank", pr_engine="gather", **pr_kw).elapsed_ms for _ in range(2))
+    detail["pagerank"]["gather_engine_ms"] = round(gather, 3)
+    hmsg = int(runs["hashmin"][0].messages.sum())
+    detail["hashmin"] = {"gteps": round(hmsg / (hm_ms * 1e-3) / 1e9, 2), "ms": round(hm_ms, 3),
+                         "supersteps": runs["hashmin"][0].supersteps, "messages": hmsg, "edges": Es,
+                         "modes": runs["hashmin"][0].mode[1:].tolist(),
+                         "policy_ms": policy_times(H, "hashmin", stream, ipg)}
+    memory = [memory_report(P, "directed R-MAT 26 (PageRank, blocked layout built)"),
+              memory_report(H, "symmetrised R-MAT 26 (Hashmin)")]
+    P.close()
+    H.close()
 
     # ---------------------------------------------------------- end to end through the C ABI, host buffers
+    e2e_steps = max(1, min(args.steps, 5))
+    out_f = torch.empty(V, dtype=torch.float32).pin_memory()
+    out_u = torch.empty(V, dtype=torch.int32).pin_memory()
     e2e_ms = []
-    h2d = 4 * (V + 1) + 8 * E  # offsets, targets, weights
-    d2h = 2 * 4 * V
-    out = torch.empty(V, dtype=torch.int32).pin_memory()
-    for i in range(args.steps):
+    for i in range(e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with ipg.Graph(V, pin["row_ptr"], pin["col"], pin["w"], symmetric=True, stream=stream) as H:
-            H.run("hashmin", **opts)
-            H.values(out=out, stream=stream)
-            H.run("sssp", source=0, **opts)
-            H.values(out=out, stream=stream)
+        with ipg.Graph(V, pin["d_ptr"], pin["d_col"], stream=stream) as A:
+            A.run("pagerank", **pr_kw)
+            A.values(out=out_f, stream=stream)
+        with ipg.Graph(V, pin["s_ptr"], pin["s_col"], symmetric=True, stream=stream) as B:
+            B.run("hashmin", **hm_kw)
+            B.values(out=out_u, stream=stream)
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = (msgs / args.steps) / (statistics.median(e2e_ms) * 1e-3) / 1e9
+    h2d = 4 * (V + 1) + 4 * Ed + 4 * (V + 1) + 4 * Es
+    e2e = {"value": round((msgs / args.steps) / (statistics.median(e2e_ms) * 1e-3) / 1e9, 3), "unit": "GTEPS",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 2 * 4 * V, "steps": e2e_steps,
+           "median_step_ms": round(statistics.median(e2e_ms), 2),
+           "covers": "graph creation from pinned host CSR (device transposition, renumbering, degree bins, "
+                     "blocked layout), both runs, results copied to pinned host memory, destroy"}
+    del pin
+    ipg.release_cached_memory()
 
-    # ---------------------------------------------------------- per-app and per-policy detail
-    detail = {}
-    for app in ("hashmin", "sssp"):
-        runs = per_app[app]
-        ms = statistics.median(r.elapsed_ms for r in runs)
-        m = int(runs[0].messages.sum())
-        detail[app] = {"gteps": round(m / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 4), "supersteps": runs[0].supersteps,
-                       "messages": m, "modes": runs[0].mode[1:].tolist()}
-        pol = {}
-        for name, o in (("threshold", dict(policy="threshold")), ("pull", dict(policy="forced", forced_mode="pull")),
-                        ("push_dense", dict(policy="forced", forced_mode="push_dense")),
-                        ("push_sparse", dict(policy="forced", forced_mode="push_sparse")),
-                        ("mlp", dict(policy="mlp"))):
-            try:
-                ts = [G.run(app, stream=stream, **o).elapsed_ms for _ in range(3)]
-                pol[name] = round(min(ts), 4)
-            except ipg.IPError:
-                pol[name] = None
-        detail[app]["policy_ms"] = pol
-    # PageRank at the small configuration (R-MAT scale 16, directed, T = 30)
+    # ---------------------------------------------------------- secondary configurations
+    detail["c2_scale22"] = c2_summary(args, stream, ipg)
+    detail["c1_pagerank_scale16"] = c1_summary(stream, ipg)
+    cpu = None
+    if pool is not None:
+        cpu = cpu_oracle_baseline(pool, d)
+        pool.close()
+    return dict(value=value, total_ms=total_ms, launches=launches, roofline=roofline, e2e=e2e,
+                clocks=clk.summary(), detail=detail, V=V, Ed=Ed, Es=Es, memory=memory, cpu=cpu)
+
+
+def policy_times(G, app, stream, ipg, reps=3):
+    pol = {}
+    for name, o in (("threshold", dict(policy="threshold")), ("mlp", dict(policy="mlp")),
+                    ("pull", dict(policy="forced", forced_mode="pull")),
+                    ("push_dense", dict(policy="forced", forced_mode="push_dense")),
+                    ("push_sparse", dict(policy="forced", forced_mode="push_sparse"))):
+        try:
+            pol[name] = round(min(G.run(app, stream=stream, **o).elapsed_ms for _ in range(reps)), 4)
+        except ipg.IPError:
+            pol[name] = None
+    return pol
+
+
+def c2_summary(args, stream, ipg, steps=10):
+    g = c2_graph()
+    out = {"workload": C2_WORKLOAD, "vertices": g.n, "edges": g.m}
+    with ipg.Graph.from_inputs(g, stream=stream) as G:
+        for app, kw in (("hashmin", {}), ("sssp", dict(source=0))):
+            rs = [G.run(app, policy=args.policy, stream=stream, **kw) for _ in range(steps + 2)][2:]
+            ms = statistics.median(r.elapsed_ms for r in rs)
+            m = int(rs[0].messages.sum())
+            out[app] = {"gteps": round(m / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 4), "supersteps": rs[0].supersteps,
+                        "messages": m, "modes": rs[0].mode[1:].tolist(),
+                        "policy_ms": policy_times(G, app, stream, ipg)}
+        out["memory"] = memory_report(G, "symmetrised weighted R-MAT 22")
+    tot = out["hashmin"]["ms"] + out["sssp"]["ms"]
+    out["gteps_step"] = round((out["hashmin"]["messages"] + out["sssp"]["messages"]) / (tot * 1e-3) / 1e9, 2)
+    return out
+
+
+def c1_summary(stream, ipg):
     import inputs
     pg = inputs.rmat_graph(16, seed=1)
     with ipg.Graph.from_inputs(pg, stream=stream) as P:
         ts = [P.run("pagerank", stream=stream, policy="forced", forced_mode="pull").elapsed_ms for _ in range(5)]
-        pr_ms = min(ts)
-    detail["pagerank_scale16"] = {"gteps": round(30 * pg.m / (pr_ms * 1e-3) / 1e9, 2), "ms": round(pr_ms, 4),
-                                  "edges": pg.m}
-    G.close()
-    return dict(value=value, total_ms=total_ms, msgs=msgs_all, launches=launches, roofline=roofline,
-                e2e=dict(value=round(e2e_value, 3), unit="GTEPS", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
-                         median_step_ms=round(statistics.median(e2e_ms), 3)),
-                clocks=clk.summary(), detail=detail, V=V, E=E, kernels={k: [round(v[0], 3), v[2]] for k, v in kern.items()})
+        mem = memory_report(P, "directed R-MAT 16")
+    pr_ms = min(ts)
+    return {"gteps": round(30 * pg.m / (pr_ms * 1e-3) / 1e9, 2), "ms": round(pr_ms, 4), "edges": pg.m,
+            "memory": mem}
 
 
-# ----------------------------------------------------------------- CPU oracle (baseline and reference arm)
-def oracle_step(g):
-    import oracle
-    t0 = time.perf_counter()
-    _, a = oracle.hashmin(g.n, g.row_ptr, g.col)
-    _, b = oracle.sssp(g.n, g.row_ptr, g.col, g.w, source=0)
-    dt = time.perf_counter() - t0
-    return int(a["messages"].sum()) + int(b["messages"].sum()), dt
-
-
-def cpu_oracle_pagerank(g, T, sample):
-    """The FP64 oracle's PageRank on the host cores (single-threaded), GTEPS = T*E / s."""
-    import oracle
-    t0 = time.perf_counter()
-    oracle.pagerank(g.n, g.row_ptr, g.col, T=T)
-    dt = time.perf_counter() - t0
-    return {"value": round(T * g.m / dt / 1e9, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample,
-            "seconds": round(dt, 2)}
-
-
-def cpu_baseline(g):
-    m, dt = oracle_step(g)
-    return {"value": round(m / dt / 1e9, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": "one full step: Hashmin + SSSP(source 0) on the same scale-22 graph, single-threaded",
-            "seconds": round(dt, 2)}
-
-
+# ----------------------------------------------------------------- reference arm (the CPU oracle)
 def run_reference(args):
-    g = build_graph(args.scale)
-    for _ in range(args.warmup):  # warm-up: the Hashmin half of a step (the oracle has no state to warm)
-        import oracle
-        oracle.hashmin(g.n, g.row_ptr, g.col)
-    msgs, secs = 0, 0.0
-    for _ in range(args.steps):
-        m, dt = oracle_step(g)
-        msgs += m
-        secs += dt
-    value = msgs / secs / 1e9
+    d, _ = c5_graphs(args.scale, symmetric=False)
+    pool = OraclePool(d, host_cores())
+    for _ in range(args.warmup):
+        pool.superstep()
+    secs = [pool.superstep() for _ in range(args.steps)]
+    pool.close()
+    value = args.steps * d.m / sum(secs) / 1e9
+    sample = (f"every step: one PageRank superstep (Fig. 8, FP64 oracle) over all {d.n:,} vertices and {d.m:,} "
+              f"edges of directed R-MAT scale {args.scale}, static vertex ranges over {pool.workers} host cores; "
+              "Hashmin not sampled")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "GTEPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * secs / args.steps, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "scale": args.scale, "policy": "oracle (push, literal Pregel)"},
-            "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                             "sample": "every step: Hashmin + SSSP(source 0) on the full scale-22 graph"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(secs) / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "scale": args.scale, "vertices": d.n, "edges": d.m,
+                       "policy": "oracle (literal Pregel PageRank superstep)"},
+            "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": pool.workers, "kind": "oracle",
+                             "sample": sample, "host_cores": host_cores()},
             "e2e": {"value": round(value, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- secondary configurations
 def ncu_case(spec, scale):
     """Small profiling case: one app in one forced mode, host-driven loop (ncu cannot
     profile kernels inside graphs with conditional nodes), run twice; or
@@ -405,7 +553,7 @@ def ncu_case(spec, scale):
         import inputs
         g = inputs.rmat_graph(scale, edge_factor=EDGE_FACTOR, a=0.57, b=0.19, c=0.19, seed=1)
     else:
-        g = build_graph(scale)
+        g = c2_graph(scale)
     if app == "batch_sssp":
         import inputs
         k = int(mode)
@@ -426,28 +574,59 @@ def ncu_case(spec, scale):
                       "ms": round(st.elapsed_ms, 4)}))
 
 
-def pr_measure(G, V, E, reps=3, T=30, engine="auto"):
-    """PageRank pull, T iterations: device time of the run and the roofline of its
-    pull exchange (the CSC gather k_pr_pull, or the blocked pull's two launches
-    k_pb_scatter + k_pb_accumulate): algorithmic bytes 8E + 16V + 4(V+1) per
-    superstep (in-edge indices and their sources' broadcasts; offsets, ranks,
-    broadcasts, out-degrees) over the exchange time, CUDA events per superstep."""
-    peak, kind = measured_peaks()
-    kw = dict(policy="forced", forced_mode="pull", pr_iterations=T, pr_engine=engine)
-    ts = [G.run("pagerank", **kw).elapsed_ms for _ in range(reps)]
-    st = G.run("pagerank", profile_kernels=1, **kw)
-    kms = [float(x) for x in st.kernel_ms[1:st.supersteps, 1]]
-    by = 4 * (V + 1) + 8 * E + 16 * V
-    avg = sum(kms) / len(kms)
-    ach = by / (avg * 1e-3) / 1e9
-    blocked = engine == "blocked" or (engine == "auto" and E >= 1 << 24)
-    kern = "k_pb_scatter+k_pb_accumulate" if blocked else "k_pr_pull"
-    return {"engine": "blocked" if blocked else "gather", "gteps": round(T * E / (min(ts) * 1e-3) / 1e9, 2),
-            "ms": round(min(ts), 4), "ms_per_iteration": round(min(ts) / T, 4),
-            "roofline": {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": peak,
-                         "peak_kind": kind, "unit": "GB/s", "frac": round(ach / peak, 4),
-                         "traffic": measured_traffic(kern) if E >= 10**9 else None,  # captured at scale 26
-                         "avg_launch_us": round(1e3 * avg, 2), "bytes_per_launch": by}}
+def c2_line(args, steps):
+    """The Hashmin + SSSP configuration on its own line, with the roofline of its
+    dominant kernel (per-kernel CUDA events in a host-driven replay of the timed
+    runs' mode sequences)."""
+    import torch
+    import paper_2010_08781_gb300 as ipg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    g = c2_graph(args.scale if args.scale != SCALE else C2_SCALE)
+    V, E = g.n, g.m
+    with ipg.Graph.from_inputs(g, stream=stream) as G:
+        def step():
+            return G.run("hashmin", policy=args.policy, stream=stream), G.run("sssp", policy=args.policy,
+                                                                                stream=stream)
+        for _ in range(3):
+            step()
+        clk = ClockSampler(0).__enter__()
+        torch.cuda.synchronize()
+        clk.start()
+        rs = [step() for _ in range(steps)]
+        torch.cuda.synchronize()
+        clk.stop()
+        clk.__exit__(None, None, None)
+        ms = sum(a.elapsed_ms + b.elapsed_ms for a, b in rs)
+        msgs = sum(int(a.messages.sum()) + int(b.messages.sum()) for a, b in rs)
+        kern = {}
+        peak, kind = measured_peaks()
+        for app, last in (("hashmin", rs[-1][0]), ("sssp", rs[-1][1])):
+            seq = last.mode[1:last.supersteps].tolist()
+            st = G.run(app, profile_kernels=1, stream=stream, mode_sequence=seq)
+            for s in range(1, st.supersteps):
+                mode = int(st.mode[s])
+                name = KERNEL_NAMES[(MODE_NAMES[mode], app)]
+                by = exchange_bytes(app, mode, V, E, int(st.messages[s - 1]), int(st.broadcasters[s - 1]),
+                                    int(st.active[s]))
+                k = kern.setdefault(name, [0.0, 0.0, 0])
+                k[0] += float(st.kernel_ms[s, 1])
+                k[1] += by
+                k[2] += 1
+        dom = max(kern, key=lambda n: kern[n][0])
+        d_ms, d_by, d_n = kern[dom]
+        ach = d_by / (d_ms * 1e-3) / 1e9
+        line = {"config": "c2", "workload": C2_WORKLOAD, "vertices": V, "edges": E,
+                "gteps": round(msgs / (ms * 1e-3) / 1e9, 3), "ms_per_step": round(ms / steps, 4),
+                "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak,
+                             "peak_kind": kind, "unit": "GB/s", "frac": round(ach / peak, 4),
+                             "avg_launch_us": round(1e3 * d_ms / d_n, 2), "launches": d_n,
+                             "traffic": stored_traffic(dom)},
+                "kernel_ms": {k: [round(v[0], 3), v[2]] for k, v in kern.items()}, "clocks": clk.summary()}
+        for app, idx in (("hashmin", 0), ("sssp", 1)):
+            line[app] = {"ms": round(statistics.median(r[idx].elapsed_ms for r in rs), 4),
+                         "modes": rs[-1][idx].mode[1:].tolist(), "policy_ms": policy_times(G, app, stream, ipg)}
+    print(json.dumps(line), flush=True)
 
 
 def run_config(args):
@@ -456,14 +635,51 @@ def run_config(args):
     import inputs
     import torch
     torch.cuda.set_device(0)
+    if args.config == "c2":
+        c2_line(args, max(args.steps, 5))
+        return
     out = {"config": args.config}
     if args.config == "c1":  # PageRank, directed R-MAT scale 16, T = 30
+        out.update(c1_summary(None, ipg))
         g = inputs.rmat_graph(16, seed=1)
-        with ipg.Graph.from_inputs(g) as G:
-            out["pagerank"] = pr_measure(G, g.n, g.m)
-        out["cpu_oracle"] = cpu_oracle_pagerank(g, 30, "PageRank T=30 on the full graph")
+        t0 = time.perf_counter()
+        import oracle
+        oracle.pagerank(g.n, g.row_ptr, g.col, T=30)
+        dt = time.perf_counter() - t0
+        out["cpu_oracle"] = {"value": round(30 * g.m / dt / 1e9, 5), "unit": "GTEPS", "cores": 1,
+                             "kind": "oracle", "sample": "PageRank T=30 on the full graph", "seconds": round(dt, 2)}
         out["workload"] = "PageRank T=30 on directed R-MAT scale 16 (edge factor 16, seed 1)"
-        out["edges"] = g.m
+    elif args.config == "bfs_perm":
+        # unit-weight SSSP (Fig. 10 exactly) with and without the early-exit pull, and what the
+        # degree-class renumbering does on a graph whose vertex ids were randomly permuted
+        sc = args.scale if args.scale != SCALE else C2_SCALE
+        g = inputs.rmat_graph(sc, edge_factor=EDGE_FACTOR, symmetrize=True, seed=1)
+        src = int(np.argmax(g.out_degree()))
+        with ipg.Graph.from_inputs(g) as G:
+            b = {}
+            for name, kw in (("pull_early_exit", dict(policy="forced", forced_mode="pull")),
+                             ("pull_full_scan", dict(policy="forced", forced_mode="pull", pull_early_exit=0)),
+                             ("threshold_early_exit", dict(policy="threshold")),
+                             ("threshold_full_scan", dict(policy="threshold", pull_early_exit=0))):
+                rs = [G.run("sssp", source=src, **kw) for _ in range(4)][1:]
+                ms = min(r.elapsed_ms for r in rs)
+                b[name] = {"ms": round(ms, 4), "gteps": round(int(rs[0].messages.sum()) / (ms * 1e-3) / 1e9, 2),
+                           "supersteps": rs[0].supersteps, "modes": rs[0].mode[1:].tolist()}
+        out["unit_weight_sssp"] = dict(b, workload=f"unit-weight SSSP from the largest hub on symmetrised R-MAT {sc}",
+                                       edges=g.m)
+        rows = {}
+        for label, gg in (("ids_as_generated", c2_graph(sc)),
+                          ("ids_permuted", inputs.rmat_graph(sc, edge_factor=EDGE_FACTOR, symmetrize=True, seed=1,
+                                                             weighted=True, wseed=1, permute_seed=7))):
+            for relabel in (False, True):
+                with ipg.Graph.from_inputs(gg, relabel=relabel) as G:
+                    r = {}
+                    for app, kw in (("hashmin", {}), ("sssp", dict(source=0))):
+                        rs = [G.run(app, policy="threshold", **kw) for _ in range(4)][1:]
+                        r[app + "_ms"] = round(min(x.elapsed_ms for x in rs), 4)
+                    rows[f"{label}/{'renumbered' if relabel else 'caller_order'}"] = r
+        out["renumbering"] = dict(rows, workload=f"Hashmin + SSSP(0), threshold policy, symmetrised weighted R-MAT {sc}")
+        out["workload"] = "unit-weight SSSP early exit; degree-class renumbering on a randomly permuted R-MAT"
     elif args.config == "c4":  # batched
         g = inputs.rmat_graph(20, symmetrize=True, weighted=True, seed=1)
         src = np.concatenate([[0], inputs.uniform_vertices(g.n, 255, seed=1)]).astype(np.uint32)
@@ -492,33 +708,13 @@ def run_config(args):
                                 "persistent_engine_ms": round(pers, 3), "ip_run_union_ms": round(single, 3)}
         out["workload"] = ("256 SSSP sources on symmetrised weighted R-MAT scale 20; 1,000 Hashmin instances, "
                            "R-MAT 1k-100k vertices (log-uniform), edge factor 8, symmetrised")
-    elif args.config == "c5":  # billion-edge
-        g = inputs.rmat_graph(26, seed=1)
-        V, E = g.n, g.m
-        out["cpu_oracle_pagerank"] = cpu_oracle_pagerank(g, 1, "PageRank with T=1 (one rank update) on the full graph")
-        with ipg.Graph(V, g.row_ptr, g.col) as G:  # in-edges transposed on the device
-            del g
-            out["pagerank"] = pr_measure(G, V, E, reps=2)
-            out["pagerank"]["vertices"], out["pagerank"]["edges"] = V, E
-            out["pagerank_gather"] = pr_measure(G, V, E, reps=2, engine="gather")
-        src, dst = inputs.rmat_edges(26, 16 << 26, seed=1)
-        gs = inputs.from_edges(1 << 26, src, dst, symmetrize=True)
-        del src, dst
-        with ipg.Graph.from_inputs(gs) as G:
-            ts = [G.run("hashmin") for _ in range(2)]
-        best = min(ts, key=lambda r: r.elapsed_ms)
-        m = int(best.messages.sum())
-        out["hashmin_symmetrised"] = {"vertices": gs.n, "edges": gs.m, "ms": round(best.elapsed_ms, 3),
-                                      "supersteps": best.supersteps, "gteps": round(m / (best.elapsed_ms * 1e-3) / 1e9, 2),
-                                      "modes": best.mode[1:].tolist()}
-        out["workload"] = "R-MAT scale 26, edge factor 16, seed 1: PageRank T=30 pull (directed), Hashmin (symmetrised)"
     print(json.dumps(out), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--scale", type=int, default=SCALE)
@@ -526,8 +722,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", default=None,
                     help="APP:MODE[:ENGINE], e.g. sssp:pull or pagerank:pull:blocked — small profiling case only")
-    ap.add_argument("--config", default=None, choices=["c1", "c4", "c5"],
-                    help="secondary configurations: c1 PageRank scale 16, c4 batched, c5 scale 26")
+    ap.add_argument("--config", default=None, choices=["c1", "c2", "c4", "bfs_perm"],
+                    help="secondary configurations: c1 PageRank scale 16, c2 Hashmin + SSSP scale 22, c4 batched, "
+                         "bfs_perm unit-weight SSSP early exit and renumbering on a permuted R-MAT")
     args = ap.parse_args()
     if args.config:
         run_config(args)
@@ -553,15 +750,17 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": round(r["value"], 3), "unit": "GTEPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["total_ms"] / args.steps, 4),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "scale": args.scale, "vertices": r["V"], "edges": r["E"],
-                           "policy": args.policy, "l2": "flushed between timed steps; inputs (1.03 GB) exceed L2",
+                "config": {"workload": WORKLOAD, "scale": args.scale, "vertices": r["V"],
+                           "edges_directed": r["Ed"], "edges_symmetrised": r["Es"], "pagerank_iterations": T_PR,
+                           "pagerank_engine": "blocked pull", "hashmin_policy": args.policy,
+                           "l2": "flushed between timed steps; inputs (about 13 GB) exceed L2",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": r["roofline"], "e2e": r["e2e"], "gpu_launches": r["launches"], "clocks": r["clocks"],
-                "per_app": r["detail"], "kernel_ms_by_name": r["kernels"]}
-        if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(build_graph(args.scale))
+                "per_app": r["detail"], "memory": r["memory"]}
+        if r["cpu"] is not None:
+            line["cpu_baseline"] = r["cpu"]
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
