@@ -108,6 +108,17 @@ typedef struct {
                                      ip_run_stats_t.kernel_ms. Values are unchanged. */
     void* stream;                 /* cudaStream_t */
     int32_t pr_engine;            /* ip_pr_engine_t (default IP_PR_ENGINE_AUTO) */
+    float pr_tolerance;           /* PageRank to convergence (the paper's Section 6.1 notes that a
+                                     real PageRank runs until convergence): > 0 ends the run after
+                                     the first superstep s >= 1 whose L1 rank change
+                                     sum_v |rank_s(v) - rank_(s-1)(v)| is below it (summed in FP32
+                                     per thread, FP64 across threads); T still caps the run.
+                                     0 (default): T updates exactly. */
+    int32_t pull_early_exit;      /* unit-weight SSSP (no weights given: Fig. 10 exactly), PULL mode:
+                                     1 (default) stops scanning a vertex's in-edges at the first one
+                                     whose source broadcast in the last superstep — all of them
+                                     carry the same distance under synchronous supersteps, so the
+                                     result is the same; 0 scans every in-edge. Ignored otherwise. */
 } ip_options_t;
 
 /* Per-run statistics. The caller owns the arrays; `capacity` is their length in
@@ -129,6 +140,8 @@ typedef struct {
                               k = 0 queue compaction, 1 exchange, 2 apply, 3 selector
                               (profile_kernels only; 0 for kernels that did not run) */
     float elapsed_ms;      /* device time of the whole run (init to halt) */
+    float* pr_delta;       /* [s]: PageRank with pr_tolerance > 0: L1 rank change of superstep s
+                              (0 for superstep 0 and for runs without a tolerance) */
 } ip_run_stats_t;
 
 /* Graph facts for callers and tests. */
@@ -140,7 +153,20 @@ typedef struct {
     uint32_t csc_is_csr;      /* 1 when the in-edge arrays alias the out-edge arrays */
     uint32_t weighted;
     uint32_t num_sms;         /* SMs of the device the graph lives on */
-    uint64_t device_bytes;    /* device memory held by the handle */
+    uint64_t device_bytes;    /* device memory held by the handle, the sum of the parts below */
+    /* Where those bytes go (the analogue of the paper's memory-footprint study,
+     * Section 7.2 and Table 3; the combined one-slot mailbox of Section 4.3.3 is
+     * one 4-byte word per vertex): */
+    uint64_t bytes_graph;         /* CSR and CSC offsets, indices and weights (the CSC shares
+                                     the CSR's arrays for a symmetric graph) */
+    uint64_t bytes_vertex_state;  /* per-vertex values, ranks, broadcast slots, mailboxes,
+                                     out-degree reciprocals, bitmaps and frontier queues */
+    uint64_t bytes_degree_bins;   /* degree-binned schedules of both edge directions (every
+                                     cached cutoff pair) */
+    uint64_t bytes_blocked_layout;/* the blocked PageRank pull's second edge layout (0 until a
+                                     run builds it) */
+    uint64_t bytes_renumbering;   /* the two vertex maps of ip_graph_relabel */
+    uint64_t bytes_other;         /* batched-run state, run logs, selector, control block */
 } ip_graph_info_t;
 
 /* ------------------------------------------------------------ entry points */
@@ -171,9 +197,15 @@ int ip_graph_create(ip_graph_t** out, uint32_t n_vertices, uint64_t n_edges, con
                     const uint32_t* csr_cols, const uint32_t* csr_weights, const uint32_t* csc_offsets,
                     const uint32_t* csc_rows, const uint32_t* csc_weights, int device_ptrs, void* stream);
 
-/* Frees every device buffer of the handle. NULL is ignored. */
+/* Releases the graph store and the run state of the handle (the vertex and
+ * edge arrays of Section 4.2, the mailboxes of Section 4.3.3 and everything the
+ * library built for them). Synchronises the graph's device once; the buffers go
+ * to the library's device-buffer cache (ip_release_cached_memory). NULL is
+ * ignored; the handle must not be used afterwards. */
 void ip_graph_destroy(ip_graph_t* g);
 
+/* Facts of the graph and of the device memory its handle holds (struct above).
+ * IP_E_INVAL for a NULL argument. */
 int ip_graph_info(const ip_graph_t* g, ip_graph_info_t* info);
 
 /* Renumbers the graph's vertices inside the handle by decreasing out-degree
@@ -203,9 +235,14 @@ int ip_graph_relabel(ip_graph_t* g, void* stream);
 int ip_run(ip_graph_t* g, ip_app_t app, uint32_t max_supersteps, const ip_options_t* opt,
            ip_run_stats_t* stats);
 
-/* Copies the values of the last run: n_vertices FP32 ranks (PageRank) or
- * uint32 labels / distances. dst_bytes must be >= 4 * n_vertices.
- * IP_E_STATE if nothing has run yet. */
+/* Copies the result of the last run: the vertex values once the run has ended
+ * (Section 4.2: global halt, when every vertex has voted to halt and no message
+ * is in flight; or the superstep cap): n_vertices FP32 ranks (PageRank, Fig. 8)
+ * or uint32 labels (Hashmin, Fig. 9) / distances (SSSP, Fig. 10), indexed by the
+ * caller's vertex ids. dst is host memory (dst_is_device = 0) or device memory
+ * (1) the caller owns; dst_bytes must be >= 4 * n_vertices (IP_E_RANGE).
+ * Synchronises the stream. IP_E_STATE if nothing has run yet, or after a batched
+ * Hashmin run (which uses the value array as scratch). */
 int ip_get_values(ip_graph_t* g, void* dst, size_t dst_bytes, int dst_is_device, void* stream);
 
 /* Loads the learned mode selector (a trained 8-32-32-3 MLP) into the handle.

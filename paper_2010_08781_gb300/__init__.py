@@ -50,7 +50,8 @@ class Options(ctypes.Structure):
                 ("mode_sequence", ctypes.POINTER(ctypes.c_uint8)), ("mode_sequence_len", ctypes.c_uint32),
                 ("t1", ctypes.c_uint32), ("t2", ctypes.c_uint32), ("thr_sparse", ctypes.c_float),
                 ("thr_pull", ctypes.c_float), ("use_graph", ctypes.c_int32), ("collect_labels", ctypes.c_int32),
-                ("profile_kernels", ctypes.c_int32), ("stream", ctypes.c_void_p), ("pr_engine", ctypes.c_int32)]
+                ("profile_kernels", ctypes.c_int32), ("stream", ctypes.c_void_p), ("pr_engine", ctypes.c_int32),
+                ("pr_tolerance", ctypes.c_float), ("pull_early_exit", ctypes.c_int32)]
 
 
 class RunStatsC(ctypes.Structure):
@@ -58,7 +59,7 @@ class RunStatsC(ctypes.Structure):
                 ("mode", ctypes.POINTER(ctypes.c_uint8)), ("active", _U32P), ("broadcasters", _U32P),
                 ("messages", ctypes.POINTER(ctypes.c_uint64)), ("features", ctypes.POINTER(ctypes.c_float)),
                 ("mode_ms", ctypes.POINTER(ctypes.c_float)), ("kernel_ms", ctypes.POINTER(ctypes.c_float)),
-                ("elapsed_ms", ctypes.c_float)]
+                ("elapsed_ms", ctypes.c_float), ("pr_delta", ctypes.POINTER(ctypes.c_float))]
 
 
 class BatchStatsC(ctypes.Structure):
@@ -70,7 +71,10 @@ class BatchStatsC(ctypes.Structure):
 class GraphInfo(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_uint32), ("n_edges", ctypes.c_uint64), ("max_out_degree", ctypes.c_uint32),
                 ("max_in_degree", ctypes.c_uint32), ("csc_is_csr", ctypes.c_uint32), ("weighted", ctypes.c_uint32),
-                ("num_sms", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64)]
+                ("num_sms", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("bytes_graph", ctypes.c_uint64),
+                ("bytes_vertex_state", ctypes.c_uint64), ("bytes_degree_bins", ctypes.c_uint64),
+                ("bytes_blocked_layout", ctypes.c_uint64), ("bytes_renumbering", ctypes.c_uint64),
+                ("bytes_other", ctypes.c_uint64)]
 
 
 _lib = None
@@ -240,6 +244,7 @@ class RunStats:
     features: np.ndarray
     mode_ms: np.ndarray
     kernel_ms: np.ndarray
+    pr_delta: np.ndarray
 
 
 class Graph:
@@ -325,7 +330,7 @@ class Graph:
         arr = dict(mode=np.zeros(cap, np.uint8), active=np.zeros(cap, np.uint32),
                    broadcasters=np.zeros(cap, np.uint32), messages=np.zeros(cap, np.uint64),
                    features=np.zeros(cap * N_FEATURES, np.float32), mode_ms=np.zeros(cap * 3, np.float32),
-                   kernel_ms=np.zeros(cap * 4, np.float32))
+                   kernel_ms=np.zeros(cap * 4, np.float32), pr_delta=np.zeros(cap, np.float32))
         s = RunStatsC()
         s.capacity = cap
         s.mode = arr["mode"].ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
@@ -335,13 +340,15 @@ class Graph:
         s.features = arr["features"].ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         s.mode_ms = arr["mode_ms"].ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         s.kernel_ms = arr["kernel_ms"].ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        s.pr_delta = arr["pr_delta"].ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         code = load().ip_run(self._h, app, int(max_supersteps), ctypes.byref(o), ctypes.byref(s))
         if code not in (IP_OK, IP_E_MAXSTEPS) or (raise_on_maxsteps and code == IP_E_MAXSTEPS):
             raise IPError(code, "ip_run")
         n = min(s.supersteps, cap)
         return RunStats(code, s.supersteps, bool(s.halted), s.elapsed_ms, arr["mode"][:n], arr["active"][:n],
                         arr["broadcasters"][:n], arr["messages"][:n], arr["features"].reshape(cap, N_FEATURES)[:n],
-                        arr["mode_ms"].reshape(cap, 3)[:n], arr["kernel_ms"].reshape(cap, 4)[:n])
+                        arr["mode_ms"].reshape(cap, 3)[:n], arr["kernel_ms"].reshape(cap, 4)[:n],
+                        arr["pr_delta"][:n])
 
     def values(self, app=None, out=None, stream=None):
         """Values of the last run: float32 ranks or uint32 labels/distances.

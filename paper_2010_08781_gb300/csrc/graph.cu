@@ -829,6 +829,8 @@ void ip_options_default(ip_options_t* o) {
     o->collect_labels = 0;
     o->stream = nullptr;
     o->pr_engine = IP_PR_ENGINE_AUTO;
+    o->pr_tolerance = 0.0f;
+    o->pull_early_exit = 1;
 }
 
 void ip_graph_destroy(ip_graph_t* g) {
@@ -909,6 +911,24 @@ int ip_graph_info(const ip_graph_t* g, ip_graph_info_t* info) {
     info->weighted = g->weighted ? 1u : 0u;
     info->num_sms = (uint32_t)g->num_sms;
     info->device_bytes = g->device_bytes;
+    // the parts, from the sizes create(), ensure_bins(), ip_graph_relabel() and pb.cu allocate
+    const uint64_t nv = g->V, ea = edge_alloc_count(g->E);
+    const uint64_t one_dir = (nv + 1) * 4 + ea * 4 * (g->weighted ? 2 : 1);
+    info->bytes_graph = g->csr_off ? one_dir * (g->csc_alias ? 1 : 2) : 0;
+    uint64_t vs = 13 * nv * 4 + 3 * (uint64_t)g->W * 4;  // 13 vertex arrays, recv + 2 broadcast bitmaps
+    vs += 2 * (uint64_t)(g->hq_cap + 1) * sizeof(uint2);
+    if (g->snap_value) vs += nv * 8;
+    info->bytes_vertex_state = g->value ? vs : 0;
+    uint64_t bins = 0;
+    for (const BinSet* S : g->binsets)
+        for (int k = 0; k < 2; ++k)
+            for (int i = 0; i < 5; ++i) bins += S->bytes[k][i];
+    info->bytes_degree_bins = bins;
+    info->bytes_blocked_layout = pb_bytes(g);
+    info->bytes_renumbering = g->new_of_old ? 2 * nv * 4 : 0;
+    const uint64_t known = info->bytes_graph + info->bytes_vertex_state + info->bytes_degree_bins +
+                           info->bytes_blocked_layout + info->bytes_renumbering;
+    info->bytes_other = g->device_bytes > known ? g->device_bytes - known : 0;
     return IP_OK;
 }
 

@@ -41,6 +41,7 @@ struct DevCtl {
     unsigned int prev_bcast;
     unsigned int pr_stale;  // PageRank: the broadcasts of the last superstep were not written (blocked pull)
     unsigned long long t_prev;  // %globaltimer at the previous selector call
+    double pr_delta;        // PageRank with a tolerance: sum over vertices of |rank change| this superstep
 };
 
 // One record per superstep, written by the selector kernel.
@@ -51,6 +52,7 @@ struct LogRec {
     unsigned int max_deg;
     unsigned long long msgs;
     float feat[N_FEATURES];
+    float pr_delta;  // PageRank: L1 rank change of the superstep (tolerance runs; 0 otherwise)
 };
 
 // Learned selector parameters on the device (layout of IP_SELECTOR_BYTES).
@@ -134,6 +136,8 @@ struct Params {
     float thr_sparse, thr_pull;
     uint32_t app, T, source, max_supersteps;
     float damping, pr_base;  // pr_base = (1-d)/N rounded to float
+    float pr_tol;            // PageRank to convergence: halt once the L1 rank change is below this (0: off)
+    uint32_t pull_early_exit;  // unit-weight SSSP: pull stops at the first broadcasting in-neighbour
     int32_t policy, forced_mode;
     uint32_t seq_len;
     uint8_t seq[MAX_SEQ];
@@ -146,11 +150,22 @@ struct Params {
 };
 
 // PageRank compute() of superstep s (Fig. 8): rank from the sum of the received
-// broadcasts, then broadcast rank / out-degree while s < T.
-__device__ __forceinline__ void pr_finish(const Params& P, uint32_t v, float sum, uint32_t s, float* nxt) {
+// broadcasts, then broadcast rank / out-degree while s < T. With a tolerance, the
+// rank's change is added to the calling thread's L1 partial dacc.
+__device__ __forceinline__ void pr_finish(const Params& P, uint32_t v, float sum, uint32_t s, float* nxt,
+                                          float& dacc) {
     const float r = fmaf(P.damping, sum, P.pr_base);  // (1-d)/N + d * sum
+    if (P.pr_tol > 0.f) dacc += fabsf(r - P.rank[v]);
     P.rank[v] = r;
     nxt[v] = s < P.T ? r * P.inv_outdeg[v] : 0.0f;
+}
+
+// Adds the calling warp's L1 partials to the superstep's rank change (all 32 lanes
+// call; nothing when no tolerance is set).
+__device__ __forceinline__ void flush_delta(const Params& P, float dacc) {
+    if (!(P.pr_tol > 0.f)) return;
+    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_down_sync(0xFFFFFFFFu, dacc, o);
+    if ((threadIdx.x & 31u) == 0 && dacc != 0.f) atomicAdd(&P.ctl->pr_delta, (double)dacc);
 }
 
 // Degree bins of both directions for one (t1, t2) pair, with their device buffers.
@@ -241,6 +256,7 @@ int pb_prepare(ip_graph* g, cudaStream_t st, PbDev* out);
 int pb_launch(const ip_graph* g, const Params& P, cudaStream_t st);
 bool pb_supported(const ip_graph* g);
 void pb_free(ip_graph* g);
+size_t pb_bytes(const ip_graph* g);  // device bytes of the blocked layout (0 if not built)
 int unpermute(const ip_graph* g, const uint32_t* in, uint32_t* out, cudaStream_t st);
 // superstep.cu
 int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* opt, ip_run_stats_t* stats);

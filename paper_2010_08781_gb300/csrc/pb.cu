@@ -255,14 +255,16 @@ __device__ __forceinline__ bool pb_mbar_wait(uint32_t bar, uint32_t parity) {
 // superstep), so this loop reads no global memory on the common path.
 __device__ __forceinline__ void pb_finish(const Params& P, uint32_t* hi, uint32_t* lo, const uint32_t* touched,
                                           uint32_t v0, uint32_t nv, uint32_t first, uint32_t stride,
-                                          float inv_scale) {
+                                          float inv_scale, float& dacc) {
     for (uint32_t v = first; v < nv; v += stride) {
         uint32_t h = 0;
         if ((touched[v >> 5] >> (v & 31)) & 1u) {
             h = __ldcg(hi + v);
             if (h) hi[v] = 0;
         }
-        P.rank[v0 + v] = fmaf(P.damping, pb_value(h, lo[v], inv_scale), P.pr_base);  // as pr_finish
+        const float r = fmaf(P.damping, pb_value(h, lo[v], inv_scale), P.pr_base);  // as pr_finish
+        if (P.pr_tol > 0.f) dacc += fabsf(r - P.rank[v0 + v]);  // tolerance runs only
+        P.rank[v0 + v] = r;
         lo[v] = 0;
     }
 }
@@ -361,6 +363,7 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
     const float inv_scale = B.inv_scale;
     const uint32_t cb0 = pb_smem(cbar), cb1 = pb_smem(cbar + 1);
     uint32_t bins_done = 0;
+    float dacc = 0.f;  // L1 rank change of the vertices this thread finishes (tolerance runs)
     for (uint32_t k = 0;; ++k) {
         const uint32_t st = k % PB_STAGES, r = k / PB_STAGES;
         if (!pb_mbar_wait(full0 + 8 * st, r & 1)) {
@@ -409,7 +412,7 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
             // the barrier also orders the high-word atomics before the reads below
             bool ok = pb_consumer_sync(cb0, bins_done & 1, lane);
             uint32_t* touched = touched2[bins_done & 1];
-            pb_finish(P, hi, acc_lo, touched, m.x, m.y, c, 32 * PB2_CONSUMERS, inv_scale);
+            pb_finish(P, hi, acc_lo, touched, m.x, m.y, c, 32 * PB2_CONSUMERS, inv_scale, dacc);
             ok = pb_consumer_sync(cb1, bins_done & 1, lane) && ok;
             // bin k+1 marks the other bitmap; this one is clear before bin k+2 starts
             for (uint32_t i = c; i < PB_BIN_V / 32; i += 32 * PB2_CONSUMERS) touched[i] = 0;
@@ -420,6 +423,7 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
             }
         }
     }
+    flush_delta(P, dacc);  // every consumer warp leaves the loop whole (warp-uniform breaks)
 }
 
 // ---------------------------------------------------------------- layout build
@@ -794,6 +798,13 @@ int pb_launch(const ip_graph* g, const Params& P, cudaStream_t st) {
     k_pb_scatter<<<L->grid1, PB1_THREADS, PB1_SMEM, st>>>(P);
     k_pb_accumulate<<<L->grid2, 32 * (PB2_CONSUMERS + 1), PB2_SMEM, st>>>(P);
     return cuda_err(cudaGetLastError());
+}
+
+size_t pb_bytes(const ip_graph* g) {
+    size_t b = 0;
+    if (g->pb)
+        for (const auto& x : static_cast<const PbLayout*>(g->pb)->bufs) b += x.second;
+    return b;
 }
 
 void pb_free(ip_graph* g) {

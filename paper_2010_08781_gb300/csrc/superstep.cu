@@ -238,6 +238,7 @@ __global__ void k_pr_init(Params P) {
         c->err = 0;
         c->prev_bcast = 0;
         c->pr_stale = 0;
+        c->pr_delta = 0.0;
         c->t_prev = globaltimer();
     }
 }
@@ -400,11 +401,22 @@ __global__ void __launch_bounds__(BLOCK) k_compact(Params P) {
 // (outbox[u] = value of u if u broadcast in the last superstep, else INF):
 // the thread at position pos of a group of `stride` threads takes blocks
 // pos, pos+stride, ...
-template <int APP>
+//
+// EARLY (unit-weight SSSP, i.e. Fig. 10 exactly): under synchronous supersteps
+// every vertex that broadcast in superstep s-1 holds the value s-1 (the
+// broadcasters of superstep k are the vertices first reached in k), so every
+// message into superstep s is s and the first broadcasting in-neighbour found
+// decides both the combined message and whether the vertex is a recipient: the
+// scan stops there (the direction-optimising pull). A group of 32 or more
+// threads runs equal trip counts and stops as a whole warp.
+template <int APP, bool EARLY = false>
 __device__ __forceinline__ void pull_range(const Params& P, uint32_t b, uint32_t e, uint32_t pos, uint32_t stride,
                                            uint32_t& m, bool& any) {
     const uint32_t bs = b >> 2, be = (e + 3) >> 2;
-    for (uint32_t g0 = bs + pos; g0 < be; g0 += stride * U) {
+    const uint32_t span = stride * U;
+    const uint32_t trips = EARLY && be > bs ? (be - bs + span - 1) / span : 0u;
+    uint32_t t = 0;
+    for (uint32_t g0 = bs + pos; EARLY ? t < trips : g0 < be; g0 += span, ++t) {
         uint4 qr[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -432,10 +444,11 @@ __device__ __forceinline__ void pull_range(const Params& P, uint32_t b, uint32_t
             for (int j = 0; j < 4; ++j)
                 if (x[u][j] != INF) m = min(m, edge_msg<APP>(x[u][j], qw, j));
         }
+        if (EARLY && (stride >= 32 ? __any_sync(FULL, any) : any)) break;
     }
 }
 
-template <int APP>
+template <int APP, bool EARLY = false>
 __global__ void __launch_bounds__(BLOCK) k_pull(Params P) {
     __shared__ uint32_t sm[BLOCK / 32];
     __shared__ uint32_t sa[BLOCK / 32];
@@ -444,7 +457,7 @@ __global__ void __launch_bounds__(BLOCK) k_pull(Params P) {
         const uint4 ch = B.hchunk[k];
         uint32_t m = INF;
         bool any = false;
-        pull_range<APP>(P, ch.y, ch.z, threadIdx.x, blockDim.x, m, any);
+        pull_range<APP, EARLY>(P, ch.y, ch.z, threadIdx.x, blockDim.x, m, any);
         m = __reduce_min_sync(FULL, m);
         const uint32_t a = __any_sync(FULL, any);
         if (lane_id() == 0) {
@@ -469,7 +482,7 @@ __global__ void __launch_bounds__(BLOCK) k_pull(Params P) {
         const uint32_t v = B.med[i];
         uint32_t m = INF;
         bool any = false;
-        pull_range<APP>(P, P.csc_off[v], P.csc_off[v + 1], lane_id(), 32, m, any);
+        pull_range<APP, EARLY>(P, P.csc_off[v], P.csc_off[v + 1], lane_id(), 32, m, any);
         m = __reduce_min_sync(FULL, m);
         any = __any_sync(FULL, any);
         if (lane_id() == 0 && any) {
@@ -484,7 +497,7 @@ __global__ void __launch_bounds__(BLOCK) k_pull(Params P) {
         bool any = false;
         if (v < P.V) {
             const uint32_t b = P.csc_off[v], e = P.csc_off[v + 1];
-            if (e - b <= P.t1) pull_range<APP>(P, b, e, 0, 1, m, any);
+            if (e - b <= P.t1) pull_range<APP, EARLY>(P, b, e, 0, 1, m, any);
         }
         if (any) P.mbox[v] = m;
         const uint32_t bits = __ballot_sync(FULL, any);
@@ -636,6 +649,7 @@ __global__ void __launch_bounds__(BLOCK) k_pr_pull(Params P) {
     const float* cur = (s & 1) ? P.contrib0 : P.contrib1;
     float* nxt = (s & 1) ? P.contrib1 : P.contrib0;
     const Bins& B = P.bin;
+    float dacc = 0.f;  // L1 rank change of the vertices this thread finishes (tolerance runs)
     for (uint32_t k = blockIdx.x; k < B.n_hchunk; k += gridDim.x) {
         const uint4 ch = B.hchunk[k];
         float a = 0.f, c = 0.f;
@@ -663,7 +677,7 @@ __global__ void __launch_bounds__(BLOCK) k_pr_pull(Params P) {
                     two_sum_acc(fa, fc, pq.x);
                     fc += pq.y;
                 }
-                pr_finish(P, ch.x, fa + fc, s, nxt);
+                pr_finish(P, ch.x, fa + fc, s, nxt, dacc);
                 B.hcnt[ch.w] = 0;
             }
         }
@@ -674,7 +688,7 @@ __global__ void __launch_bounds__(BLOCK) k_pr_pull(Params P) {
         float a = 0.f, c = 0.f;
         pr_gather(P.csc_row, cur, P.csc_off[v], P.csc_off[v + 1], lane_id(), 32, a, c);
         warp_two_sum(a, c);
-        if (lane_id() == 0) pr_finish(P, v, a + c, s, nxt);
+        if (lane_id() == 0) pr_finish(P, v, a + c, s, nxt, dacc);
     }
     const uint32_t tiles = (P.V + 31) / 32;
     for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
@@ -684,10 +698,11 @@ __global__ void __launch_bounds__(BLOCK) k_pr_pull(Params P) {
             if (e - b <= P.t1) {
                 float a = 0.f, c = 0.f;
                 pr_gather(P.csc_row, cur, b, e, 0, 1, a, c);
-                pr_finish(P, v, a + c, s, nxt);
+                pr_finish(P, v, a + c, s, nxt, dacc);
             }
         }
     }
+    flush_delta(P, dacc);
 }
 
 // PageRank push: every vertex adds value/out-degree into its out-neighbours' mailboxes.
@@ -753,11 +768,13 @@ __global__ void __launch_bounds__(BLOCK) k_pr_push(Params P) {
 __global__ void __launch_bounds__(BLOCK) k_pr_apply(Params P) {
     const uint32_t s = P.ctl->superstep;  // the superstep being computed
     float* nxt = (s & 1) ? P.contrib1 : P.contrib0;
+    float dacc = 0.f;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < P.V; v += gridDim.x * blockDim.x) {
         const float sum = P.mboxf[v];
         P.mboxf[v] = 0.0f;
-        pr_finish(P, v, sum, s, nxt);
+        pr_finish(P, v, sum, s, nxt, dacc);
     }
+    flush_delta(P, dacc);
 }
 
 // ================================================================ selector
@@ -822,8 +839,9 @@ __global__ void k_select(Params P) {
     f[6] = P.E ? (float)((double)msgs / (double)P.E) : 0.f;
     f[7] = logf(((float)bc + 1.f) / ((float)c->prev_bcast + 1.f));
     uint32_t done;
-    if (P.app == APP_PR)
-        done = s >= P.T ? 1u : 0u;
+    const double pr_delta = P.app == APP_PR ? c->pr_delta : 0.0;
+    if (P.app == APP_PR)  // T updates, or (PageRank to convergence) a superstep that changed the ranks
+        done = (s >= P.T || (P.pr_tol > 0.f && s >= 1 && pr_delta < (double)P.pr_tol)) ? 1u : 0u;  // by < tol in L1
     else
         done = msgs == 0 ? 1u : 0u;
     if (!done && s + 1 >= P.max_supersteps) done = 2;
@@ -846,6 +864,7 @@ __global__ void k_select(Params P) {
             r.max_deg = maxd;
             r.msgs = msgs;
             for (int i = 0; i < N_FEATURES; ++i) r.feat[i] = f[i];
+            r.pr_delta = (float)pr_delta;
             P.log[s] = r;
         }
         c->mode = (unsigned)mode;
@@ -861,6 +880,7 @@ __global__ void k_select(Params P) {
             c->msgs = 0;
             c->max_deg = 0;
             c->rq_len = 0;
+            c->pr_delta = 0.0;
             for (int k = 0; k < 3; ++k) c->q_len[s1 & 1][k] = 0;
         }
         if (P.use_graph) {
@@ -882,7 +902,8 @@ int grid_of(const ip_graph* g, const void* fn) {
     return g->num_sms * occ;
 }
 
-enum { G_PR_PULL, G_PR_PUSH, G_PUSH_HM_S, G_PUSH_SSSP_S, G_PUSH_HM_D, G_PUSH_SSSP_D, G_PULL_HM, G_PULL_SSSP, G_MISC, G_COUNT };
+enum { G_PR_PULL, G_PR_PUSH, G_PUSH_HM_S, G_PUSH_SSSP_S, G_PUSH_HM_D, G_PUSH_SSSP_D, G_PULL_HM, G_PULL_SSSP, G_MISC,
+       G_PULL_BFS, G_COUNT };
 
 // Grid sizes (resident CTAs per SM x SMs), queried once per handle, outside any capture.
 void compute_grids(ip_graph* g) {
@@ -890,7 +911,8 @@ void compute_grids(ip_graph* g) {
     const void* fns[G_COUNT] = {(const void*)k_pr_pull, (const void*)k_pr_push, (const void*)k_push<APP_HM, true>,
                                 (const void*)k_push<APP_SSSP, true>, (const void*)k_push<APP_HM, false>,
                                 (const void*)k_push<APP_SSSP, false>, (const void*)k_pull<APP_HM>,
-                                (const void*)k_pull<APP_SSSP>, (const void*)k_apply_bitmap};
+                                (const void*)k_pull<APP_SSSP>, (const void*)k_apply_bitmap,
+                                (const void*)k_pull<APP_SSSP, true>};
     for (int i = 0; i < G_COUNT; ++i) g->grid[i] = grid_of(g, fns[i]);
     g->grids_ready = true;
 }
@@ -952,6 +974,8 @@ int launch_superstep(const ip_graph* g, const Params& P, int mode, cudaStream_t 
             mark(1);
             if (hm)
                 k_pull<APP_HM><<<G[G_PULL_HM], BLOCK, 0, st>>>(P);
+            else if (P.pull_early_exit)  // unit weights: the first broadcasting in-neighbour decides
+                k_pull<APP_SSSP, true><<<G[G_PULL_BFS], BLOCK, 0, st>>>(P);
             else
                 k_pull<APP_SSSP><<<G[G_PULL_SSSP], BLOCK, 0, st>>>(P);
             mark(2);
@@ -1204,6 +1228,7 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     if (o.policy == IP_POLICY_MLP && !g->has_selector) return IP_E_STATE;
     if (app == APP_PR && !(o.damping >= 0.f && o.damping <= 1.f)) return IP_E_INVAL;
     if (o.pr_engine < IP_PR_ENGINE_AUTO || o.pr_engine > IP_PR_ENGINE_BLOCKED) return IP_E_INVAL;
+    if (!(o.pr_tolerance >= 0.f && o.pr_tolerance <= 3.4e38f)) return IP_E_INVAL;  // also rejects NaN
     const uint32_t t1 = o.t1 ? o.t1 : DEFAULT_T1;
     const uint32_t t2 = o.t2 ? o.t2 : DEFAULT_T2;
     if (t1 >= t2) return IP_E_INVAL;
@@ -1271,6 +1296,8 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     P.max_supersteps = max_supersteps;
     P.damping = o.damping;
     P.pr_base = (float)((1.0 - (double)o.damping) / (double)g->V);
+    P.pr_tol = app == APP_PR ? o.pr_tolerance : 0.f;
+    P.pull_early_exit = (app == APP_SSSP && !g->csc_w && o.pull_early_exit) ? 1u : 0u;
     P.policy = o.policy == IP_POLICY_AUTO ? (g->has_selector ? IP_POLICY_MLP : IP_POLICY_THRESHOLD) : o.policy;
     P.forced_mode = o.forced_mode;
     P.seq_len = o.policy == IP_POLICY_SEQUENCE ? o.mode_sequence_len : 1;
@@ -1341,6 +1368,7 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
                 if (stats->messages) stats->messages[i] = h[i].msgs;
                 if (stats->features)
                     for (int k = 0; k < N_FEATURES; ++k) stats->features[i * N_FEATURES + k] = h[i].feat[k];
+                if (stats->pr_delta) stats->pr_delta[i] = h[i].pr_delta;
             }
             free(h);
         }

@@ -53,3 +53,30 @@ def test_release_cached_memory_then_create():
             G.run("sssp")
             assert np.array_equal(G.values("sssp"), want)
         ipg.release_cached_memory()
+
+
+def test_memory_footprint_breakdown():
+    """ip_graph_info's parts add up to the handle's device bytes and each part has
+    its expected size: graph store, 13 vertex arrays plus 3 bitmaps, the two maps
+    of the renumbering, and the blocked layout once a blocked pull has run."""
+    d = inputs.rmat_graph(14, seed=3)
+    with ipg.Graph(d.n, d.row_ptr, d.col, relabel=True) as G:
+        i0 = G.info()
+        n, ea = d.n, ((d.m + 3) // 4) * 4 + 4
+        assert i0["bytes_graph"] == 2 * ((n + 1) * 4 + ea * 4)  # CSR and device-built CSC, unweighted
+        words = ((n + 31) // 32 + 31) // 32 * 32
+        assert i0["bytes_vertex_state"] >= 13 * n * 4 + 3 * words * 4
+        assert i0["bytes_renumbering"] == 8 * n
+        assert i0["bytes_degree_bins"] > 0 and i0["bytes_blocked_layout"] == 0
+        G.run("pagerank", policy="forced", forced_mode="pull", pr_engine="blocked")
+        i1 = G.info()
+        assert i1["bytes_blocked_layout"] >= 8 * d.m  # about 8 bytes per edge
+        for info in (i0, i1):
+            parts = sum(info[k] for k in info if k.startswith("bytes_"))
+            assert parts == info["device_bytes"]
+            assert info["bytes_other"] < 1 << 23  # run log (up to 65,536 supersteps), selector, control
+    s = inputs.rmat_graph(12, symmetrize=True, weighted=True, seed=3)
+    with ipg.Graph.from_inputs(s, relabel=False) as G:
+        info = G.info()
+        assert info["bytes_graph"] == (s.n + 1) * 4 + 2 * (((s.m + 3) // 4) * 4 + 4) * 4  # shared CSR/CSC, weights
+        assert info["bytes_renumbering"] == 0
