@@ -61,6 +61,8 @@ def _L():
             lib.gg_sym_weights.argtypes = [ctypes.c_uint32, U32, U32, ctypes.c_uint64, U32]
             lib.gg_uniform_vertices.argtypes = [ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64, U32]
             lib.gg_loguniform.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, U32]
+            lib.gg_random_keys.argtypes = [ctypes.c_int64, ctypes.c_uint64, U64]
+            lib.gg_random_keys.restype = None
             lib.gg_mix64.argtypes = [ctypes.c_uint64]
             lib.gg_mix64.restype = ctypes.c_uint64
             lib.gg_num_threads.restype = ctypes.c_int
@@ -172,14 +174,28 @@ def transpose(n, row_ptr, col, w=None):
     return t_ptr, t_idx[:e], (t_w[:e] if t_w is not None else None)
 
 
+def random_permutation(n: int, seed: int) -> np.ndarray:
+    """Seeded uniform random permutation of [0, n): the order that sorts the items'
+    counter-based keys (gg_random_keys); the same on every machine."""
+    keys = np.empty(max(n, 1), np.uint64)
+    _L().gg_random_keys(n, seed, _p64(keys))
+    return np.argsort(keys[:n], kind="stable").astype(np.uint32)
+
+
 def rmat_graph(scale: int, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1, symmetrize=False,
-               weighted=False, wseed=None) -> Graph:
-    """R-MAT graph: n = 2^scale, edge_factor * n drawn edges, duplicates removed."""
+               weighted=False, wseed=None, permute_seed=None) -> Graph:
+    """R-MAT graph: n = 2^scale, edge_factor * n drawn edges, duplicates removed.
+    permute_seed: relabel vertex v as perm[v] (random_permutation(n, permute_seed))
+    before assembly, so the high-degree vertices are not the low ids."""
     n = 1 << scale
     src, dst = rmat_edges(scale, edge_factor * n, a, b, c, seed)
+    if permute_seed is not None:
+        perm = random_permutation(n, permute_seed)
+        src, dst = perm[src], perm[dst]
     g = from_edges(n, src, dst, symmetrize, weighted, seed if wseed is None else wseed,
-                   name=f"rmat{scale}{'s' if symmetrize else ''}")
-    g.meta.update(kind="rmat", scale=scale, edge_factor=edge_factor, a=a, b=b, c=c, seed=seed)
+                   name=f"rmat{scale}{'s' if symmetrize else ''}{'p' if permute_seed is not None else ''}")
+    g.meta.update(kind="rmat", scale=scale, edge_factor=edge_factor, a=a, b=b, c=c, seed=seed,
+                  permute_seed=permute_seed)
     return g
 
 

@@ -15,7 +15,8 @@
  * R-MAT (Chakrabarti, Zhan and Faloutsos, SDM 2004): for each of `scale`
  * levels, from the most significant bit down, one uniform draw picks a
  * quadrant: [0,a) -> (src bit 0, dst bit 0), [a,a+b) -> (0,1),
- * [a+b,a+b+c) -> (1,0), otherwise (1,1). No noise and no vertex permutation.
+ * [a+b,a+b+c) -> (1,0), otherwise (1,1). No noise and no vertex permutation
+ * (the permuted variant relabels the vertices afterwards, see gg_random_keys).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -43,6 +44,14 @@ int gg_num_threads(void) {
 }
 
 uint64_t gg_mix64(uint64_t z) { return mix64(z); }
+
+/* key[i] = a counter-based 64-bit draw for item i (stream `seed`): sorting the
+ * items by key gives a seeded uniform random permutation. */
+void gg_random_keys(int64_t n, uint64_t seed, uint64_t* key) {
+    const uint64_t base = mix64(seed ^ 0x5065726d75746521ULL);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) key[i] = mix64(base + (uint64_t)i * GOLDEN);
+}
 
 /* R-MAT edge stream: edges [0, m) written to src/dst. */
 void gg_rmat_edges(int scale, int64_t m, double a, double b, double c, uint64_t seed,

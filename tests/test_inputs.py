@@ -56,3 +56,21 @@ def test_sources_and_sizes():
     z = inputs.loguniform_ints(1000, 1000, 100000, seed=1)
     assert z.min() >= 1000 and z.max() <= 100000
     assert np.array_equal(z, inputs.loguniform_ints(1000, 1000, 100000, seed=1))
+
+
+def test_permuted_rmat_is_the_same_graph_relabelled():
+    """The permuted variant is a seeded relabelling: a permutation, deterministic,
+    the same degree multiset and an isomorphic edge set; the hub is no longer vertex 0."""
+    p = inputs.random_permutation(1024, 7)
+    assert np.array_equal(np.sort(p), np.arange(1024)) and np.array_equal(p, inputs.random_permutation(1024, 7))
+    a = inputs.rmat_graph(10, seed=3)
+    b = inputs.rmat_graph(10, seed=3, permute_seed=7)
+    assert a.m == b.m
+    assert np.array_equal(np.sort(a.out_degree()), np.sort(b.out_degree()))
+    assert np.array_equal(b.out_degree()[p], a.out_degree())
+    sa, ta = a.edges()
+    sb, tb = b.edges()
+    ka = np.sort(p[sa].astype(np.uint64) << 32 | p[ta])
+    kb = np.sort(sb.astype(np.uint64) << 32 | tb)
+    assert np.array_equal(ka, kb)
+    assert b.out_degree().argmax() == p[0] != 0
