@@ -16,6 +16,9 @@ leg, and by nothing else. The GPU product path never imports this package.
   to check and to time one superstep of a billion-edge graph.
 * PageRank to convergence (``pagerank(..., tolerance=eps)``): the run ends after
   the first superstep whose L1 rank change is below eps.
+* ``reliability`` — the most reliable path (an application the paper does not
+  have, the GPU library's example of its vertex-program interface) in the same
+  engine: FP32 products of edge probabilities, max combiner.
 * ``mlp.py`` — FP64 forward/backward of the 8-32-32-3 mode-selector MLP.
 
 The compiled part is built on first use with gcc (``build()``).
@@ -71,7 +74,9 @@ def _L():
             lib.oracle_pagerank_superstep.restype = None
             lib.oracle_hashmin.argtypes = [ctypes.c_uint32, U32, U32, ctypes.c_uint32, U32, st]
             lib.oracle_sssp.argtypes = [ctypes.c_uint32, U32, U32, U32, ctypes.c_uint32, ctypes.c_uint32, U32, st]
-            for f in (lib.oracle_pagerank, lib.oracle_hashmin, lib.oracle_sssp):
+            lib.oracle_reliability.argtypes = [ctypes.c_uint32, U32, U32, U32, ctypes.c_uint32, ctypes.c_uint32,
+                                               ctypes.POINTER(ctypes.c_float), st]
+            for f in (lib.oracle_pagerank, lib.oracle_hashmin, lib.oracle_sssp, lib.oracle_reliability):
                 f.restype = ctypes.c_int
             _lib = lib
         return _lib
@@ -158,6 +163,20 @@ def sssp(n, row_ptr, col, w=None, source=0, max_supersteps=1 << 30, stats_cap=40
     return out[:n], _finish(r, s, arrs)
 
 
+def reliability(n, row_ptr, col, w=None, source=0, max_supersteps=1 << 30, stats_cap=4096):
+    """Most reliable path (not in the paper): FP32 value = the largest product of
+    edge probabilities w/256 over the paths from source (1/256 per edge without
+    weights), products taken along the path from the source; 0 where unreachable.
+    Returns (value[n] float32, stats)."""
+    out = np.zeros(max(n, 1), np.float32)
+    s, arrs = _stats(stats_cap)
+    rp, c = _u32(row_ptr), _u32(col)
+    wp = _u32(w).ctypes.data_as(U32) if w is not None else None
+    r = _L().oracle_reliability(n, rp.ctypes.data_as(U32), c.ctypes.data_as(U32), wp, source, max_supersteps,
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(s))
+    return out[:n], _finish(r, s, arrs)
+
+
 def run_app(app: str, g, **kw):
     """Dispatch on an app name for a graph object with row_ptr/col/w/n."""
     if app == "pagerank":
@@ -166,6 +185,8 @@ def run_app(app: str, g, **kw):
         return hashmin(g.n, g.row_ptr, g.col, **kw)
     if app == "sssp":
         return sssp(g.n, g.row_ptr, g.col, g.w, **kw)
+    if app == "reliability":
+        return reliability(g.n, g.row_ptr, g.col, g.w, **kw)
     raise ValueError(app)
 
 

@@ -32,6 +32,12 @@
  *              edge (u,v) is value(u) + w(u,v), saturating at INF
  *              (0xFFFFFFFF). With no weights every edge weighs 1, which is
  *              exactly Fig. 10.
+ *   Reliability  (not in the paper; the library's example of an application
+ *              added through its vertex-program interface) the most reliable
+ *              path from a source: edge survival probability p = w(u,v)/256
+ *              (1/256 without weights), FP32 value, message value(u) * p
+ *              rounded to FP32, max combiner; written in the shape of Fig. 10
+ *              with the comparison reversed.
  * A vertex with out-degree 0 broadcasts to nobody, so PageRank mass at
  * dangling vertices is dropped, as in the Pregel version (Fig. 12).
  */
@@ -68,6 +74,7 @@ typedef struct {
     int halted;
     double value_f; /* PageRank value */
     uint32_t value; /* Hashmin / SSSP value */
+    float value_r;  /* Reliability value */
 } vertex;
 
 /* ------------------------------------------------------- engine contexts */
@@ -82,7 +89,8 @@ struct engine {
     uint8_t* has_msg[2];
     double* box_f[2];
     uint32_t* box_u[2];
-    int sum_combiner; /* 1: PageRank (double, +); 0: min over uint32 */
+    float* box_r[2];
+    int combiner; /* COMBINE_MIN_U32, COMBINE_SUM_F64 (PageRank) or COMBINE_MAX_F32 (Reliability) */
     uint8_t* consumed; /* the current message of a vertex was already read */
     /* per-superstep counters */
     uint32_t broadcasters;
@@ -97,12 +105,18 @@ struct engine {
     double delta;
 };
 
+enum { COMBINE_MIN_U32 = 0, COMBINE_SUM_F64 = 1, COMBINE_MAX_F32 = 2 };
+
 /* Fig. 5: the min combiner. */
 static void combine_min(uint32_t* old, uint32_t new_msg) {
     if (*old > new_msg) *old = new_msg;
 }
 /* Fig. 8: the sum combiner. */
 static void combine_sum(double* old, double new_msg) { *old += new_msg; }
+/* The max combiner over FP32 (Reliability). */
+static void combine_max_f32(float* old, float new_msg) {
+    if (new_msg > *old) *old = new_msg;
+}
 
 /* Delivery of one message into the recipient's next-superstep mailbox. */
 static void deliver_u(engine* e, uint32_t dst, uint32_t msg) {
@@ -111,6 +125,15 @@ static void deliver_u(engine* e, uint32_t dst, uint32_t msg) {
         e->box_u[1][dst] = msg;
     } else {
         combine_min(&e->box_u[1][dst], msg);
+    }
+    e->messages++;
+}
+static void deliver_r(engine* e, uint32_t dst, float msg) {
+    if (!e->has_msg[1][dst]) {
+        e->has_msg[1][dst] = 1;
+        e->box_r[1][dst] = msg;
+    } else {
+        combine_max_f32(&e->box_r[1][dst], msg);
     }
     e->messages++;
 }
@@ -131,6 +154,12 @@ static int get_next_message_u(engine* e, vertex* me, uint32_t* msg) {
     if (!e->has_msg[0][me->id] || e->consumed[me->id]) return 0;
     e->consumed[me->id] = 1;
     *msg = e->box_u[0][me->id];
+    return 1;
+}
+static int get_next_message_r(engine* e, vertex* me, float* msg) {
+    if (!e->has_msg[0][me->id] || e->consumed[me->id]) return 0;
+    e->consumed[me->id] = 1;
+    *msg = e->box_r[0][me->id];
     return 1;
 }
 static int get_next_message_f(engine* e, vertex* me, double* msg) {
@@ -156,6 +185,16 @@ static void broadcast_plus_weight(engine* e, vertex* me, uint32_t base) {
     for (uint32_t k = e->g.row_ptr[me->id]; k < e->g.row_ptr[me->id + 1]; ++k) {
         uint64_t m = (uint64_t)base + (e->g.w ? e->g.w[k] : 1u);
         deliver_u(e, e->g.col[k], m >= ORACLE_INF ? ORACLE_INF : (uint32_t)m);
+    }
+}
+/* Broadcast for Reliability: the message along edge k is base * p(k) in FP32,
+ * p(k) = w[k] / 256 (w = 1 when the graph is unweighted; w * 2^-8 is exact). */
+static void broadcast_times_probability(engine* e, vertex* me, float base) {
+    e->broadcasters++;
+    for (uint32_t k = e->g.row_ptr[me->id]; k < e->g.row_ptr[me->id + 1]; ++k) {
+        const float p = (float)(e->g.w ? e->g.w[k] : 1u) * 0.00390625f;
+        const float m = base * p;
+        deliver_r(e, e->g.col[k], m);
     }
 }
 static void vote_to_halt(vertex* me) { me->halted = 1; }
@@ -216,6 +255,31 @@ static void compute_sssp(engine* e, vertex* me) {
     vote_to_halt(me);
 }
 
+/* Reliability: the source is certain and broadcasts; a larger combined
+ * probability replaces the value and is broadcast. */
+static void compute_reliability(engine* e, vertex* me) {
+    if (get_superstep(e) == 0) {
+        if (me->id == e->source) {
+            me->value_r = 1.0f;
+            broadcast_times_probability(e, me, me->value_r);
+        } else {
+            me->value_r = 0.0f;
+        }
+    } else {
+        float best = 0.0f, msg;
+        int got = 0;
+        while (get_next_message_r(e, me, &msg)) {
+            best = (!got || msg > best) ? msg : best;
+            got = 1;
+        }
+        if (got && best > me->value_r) {
+            me->value_r = best;
+            broadcast_times_probability(e, me, me->value_r);
+        }
+    }
+    vote_to_halt(me);
+}
+
 /* ---------------------------------------------------- superstep driver */
 static int run(engine* e, compute_fn compute, uint32_t max_supersteps, oracle_stats* st) {
     const uint32_t n = e->g.n;
@@ -255,10 +319,14 @@ static int run(engine* e, compute_fn compute, uint32_t max_supersteps, oracle_st
         e->has_msg[0] = e->has_msg[1];
         e->has_msg[1] = th;
         memset(e->has_msg[1], 0, n);
-        if (e->sum_combiner) {
+        if (e->combiner == COMBINE_SUM_F64) {
             double* tf = e->box_f[0];
             e->box_f[0] = e->box_f[1];
             e->box_f[1] = tf;
+        } else if (e->combiner == COMBINE_MAX_F32) {
+            float* tr = e->box_r[0];
+            e->box_r[0] = e->box_r[1];
+            e->box_r[1] = tr;
         } else {
             uint32_t* tu = e->box_u[0];
             e->box_u[0] = e->box_u[1];
@@ -283,20 +351,22 @@ static int run(engine* e, compute_fn compute, uint32_t max_supersteps, oracle_st
 }
 
 static int setup(engine* e, uint32_t n, const uint32_t* row_ptr, const uint32_t* col, const uint32_t* w,
-                 int sum_combiner) {
+                 int combiner) {
     memset(e, 0, sizeof(*e));
     e->g.n = n;
     e->g.row_ptr = row_ptr;
     e->g.col = col;
     e->g.w = w;
-    e->sum_combiner = sum_combiner;
+    e->combiner = combiner;
     size_t nn = n ? n : 1;
     e->vertices = (vertex*)calloc(nn, sizeof(vertex));
     e->consumed = (uint8_t*)calloc(nn, 1);
     for (int b = 0; b < 2; ++b) {
         e->has_msg[b] = (uint8_t*)calloc(nn, 1);
-        if (sum_combiner)
+        if (combiner == COMBINE_SUM_F64)
             e->box_f[b] = (double*)calloc(nn, sizeof(double));
+        else if (combiner == COMBINE_MAX_F32)
+            e->box_r[b] = (float*)calloc(nn, sizeof(float));
         else
             e->box_u[b] = (uint32_t*)calloc(nn, sizeof(uint32_t));
     }
@@ -315,6 +385,7 @@ static void teardown(engine* e) {
         free(e->has_msg[b]);
         free(e->box_f[b]);
         free(e->box_u[b]);
+        free(e->box_r[b]);
     }
 }
 
@@ -323,7 +394,7 @@ static void teardown(engine* e) {
 int oracle_pagerank(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, uint32_t T, double damping,
                     double tolerance, uint32_t max_supersteps, double* value_out, oracle_stats* st) {
     engine e;
-    if (setup(&e, n, row_ptr, col, NULL, 1)) return -1;
+    if (setup(&e, n, row_ptr, col, NULL, COMBINE_SUM_F64)) return -1;
     e.T = T;
     e.damping = damping;
     e.tolerance = tolerance;
@@ -336,7 +407,7 @@ int oracle_pagerank(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, ui
 int oracle_hashmin(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, uint32_t max_supersteps,
                    uint32_t* value_out, oracle_stats* st) {
     engine e;
-    if (setup(&e, n, row_ptr, col, NULL, 0)) return -1;
+    if (setup(&e, n, row_ptr, col, NULL, COMBINE_MIN_U32)) return -1;
     int r = run(&e, compute_hashmin, max_supersteps, st);
     for (uint32_t v = 0; v < n; ++v) value_out[v] = e.vertices[v].value;
     teardown(&e);
@@ -346,7 +417,7 @@ int oracle_hashmin(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, uin
 int oracle_sssp(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, const uint32_t* w, uint32_t source,
                 uint32_t max_supersteps, uint32_t* value_out, oracle_stats* st) {
     engine e;
-    if (setup(&e, n, row_ptr, col, w, 0)) return -1;
+    if (setup(&e, n, row_ptr, col, w, COMBINE_MIN_U32)) return -1;
     e.source = source;
     int r = run(&e, compute_sssp, max_supersteps, st);
     for (uint32_t v = 0; v < n; ++v) value_out[v] = e.vertices[v].value;
@@ -374,4 +445,15 @@ void oracle_pagerank_superstep(uint32_t n, const uint32_t* in_ptr, const uint32_
         }
         out[v - v_begin] = base + damping * sum;
     }
+}
+
+int oracle_reliability(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, const uint32_t* w, uint32_t source,
+                       uint32_t max_supersteps, float* value_out, oracle_stats* st) {
+    engine e;
+    if (setup(&e, n, row_ptr, col, w, COMBINE_MAX_F32)) return -1;
+    e.source = source;
+    int r = run(&e, compute_reliability, max_supersteps, st);
+    for (uint32_t v = 0; v < n; ++v) value_out[v] = e.vertices[v].value_r;
+    teardown(&e);
+    return r;
 }

@@ -459,3 +459,94 @@ def test_pagerank_convergence_matches_dense_iteration():
     got, st = oracle.pagerank(g.n, g.row_ptr, g.col, T=5, tolerance=eps)  # the cap T comes first
     assert st["halted"] and st["supersteps"] == 6
     np.testing.assert_allclose(got, r[5], rtol=1e-12)
+
+
+# ------------------------------------------------- Reliability (not in the paper)
+def _f32_prob(w):
+    return np.float32(w) * np.float32(1.0 / 256.0)
+
+
+def _best_products_brute(n, edges, weights, source):
+    """Max over all simple paths from source of the FP32 product of edge
+    probabilities taken from the source outwards (depth-first enumeration)."""
+    adj = {}
+    for (a, b), w in zip(edges, weights):
+        adj.setdefault(a, []).append((b, _f32_prob(w)))
+    best = np.zeros(n, np.float32)
+    best[source] = np.float32(1.0)
+
+    def dfs(u, val, seen):
+        for v, p in adj.get(u, []):
+            if v in seen:
+                continue
+            x = np.float32(val * p)
+            if x > best[v]:
+                best[v] = x
+            dfs(v, x, seen | {v})
+
+    dfs(source, np.float32(1.0), {source})
+    return best
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_reliability_brute_force_tiny(seed):
+    rng = np.random.default_rng(seed)
+    n = 8
+    e = {(int(a), int(b)) for a, b in zip(rng.integers(0, n, 20), rng.integers(0, n, 20)) if a != b}
+    src = [a for a, _ in sorted(e)]
+    dst = [b for _, b in sorted(e)]
+    g = inputs.from_edges(n, src, dst)
+    w = rng.integers(1, 256, g.m).astype(np.uint32)  # per-edge weights in CSR order
+    s, t = g.edges()
+    want = _best_products_brute(n, list(zip(s.tolist(), t.tolist())), w.tolist(), 0)
+    got, st = oracle.reliability(g.n, g.row_ptr, g.col, w, source=0)
+    assert np.array_equal(got, want), (got, want)
+    assert st["halted"]
+
+
+def _dijkstra_max_product(g, w, source):
+    """Dijkstra on the FP32 max-product order (a product never grows along an
+    edge, p <= 1, and FP32 rounding keeps that order)."""
+    import heapq
+    best = np.zeros(g.n, np.float32)
+    best[source] = np.float32(1.0)
+    done = np.zeros(g.n, bool)
+    heap = [(-1.0, source)]
+    while heap:
+        negv, u = heapq.heappop(heap)
+        if done[u]:
+            continue
+        done[u] = True
+        val = best[u]
+        for k in range(int(g.row_ptr[u]), int(g.row_ptr[u + 1])):
+            v = int(g.col[k])
+            x = np.float32(val * _f32_prob(w[k] if w is not None else 1))
+            if x > best[v]:
+                best[v] = x
+                heapq.heappush(heap, (-float(x), v))
+    return best
+
+
+@pytest.mark.parametrize("sym", [True, False])
+def test_reliability_dijkstra(sym):
+    g = inputs.rmat_graph(10, symmetrize=sym, weighted=True, seed=5)
+    src = int(np.argmax(g.out_degree()))
+    want = _dijkstra_max_product(g, g.w, src)
+    got, _ = oracle.reliability(g.n, g.row_ptr, g.col, g.w, source=src)
+    assert np.array_equal(got, want), int((got != want).sum())
+
+
+def test_reliability_unit_weights_are_bfs_layers():
+    """Without weights every edge keeps 1/256: a vertex at BFS depth d gets exactly
+    2^(-8d) (exact in FP32 while representable), unreachable vertices 0, and the
+    broadcasters of superstep d are the BFS layer d."""
+    from scipy.sparse.csgraph import shortest_path
+    g = inputs.rmat_graph(11, symmetrize=True, seed=3)
+    depth = shortest_path(_csr_matrix(g), unweighted=True, indices=0)
+    got, st = oracle.reliability(g.n, g.row_ptr, g.col, None, source=0)
+    reach = np.isfinite(depth)
+    assert depth[reach].max() <= 15
+    np.testing.assert_array_equal(got[reach], np.ldexp(np.float32(1.0), (-8 * depth[reach]).astype(int)))
+    assert (got[~reach] == 0).all()
+    layers = np.bincount(depth[reach].astype(int))
+    assert st["broadcasters"][:len(layers)].tolist() == layers.tolist()
