@@ -50,8 +50,14 @@ extern "C" {
 typedef enum {
     IP_PAGERANK = 0, /* Fig. 8 (constant (1-d)/N as in Fig. 12); FP32 ranks */
     IP_HASHMIN = 1,  /* Fig. 9; uint32 labels */
-    IP_SSSP = 2      /* Fig. 10 with message value(u) + w(u,v); uint32 distances,
+    IP_SSSP = 2,     /* Fig. 10 with message value(u) + w(u,v); uint32 distances,
                         unreachable = 0xFFFFFFFF */
+    IP_RELIABILITY = 3 /* not in the paper: most reliable path from ip_options_t.source, written
+                          against the vertex-program interface (include/ipregel_program.cuh);
+                          edge survival probability w(u,v) / 256 (1/256 without weights);
+                          FP32 value = the largest product of probabilities over the paths
+                          from the source, products taken along the path from the source
+                          (max combiner, CAS-combined); 0 where unreachable */
 } ip_app_t;
 
 /* How the messages broadcast in superstep s reach their recipients in s+1

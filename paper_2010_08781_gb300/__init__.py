@@ -25,8 +25,9 @@ IP_E_MAXSTEPS = -6
 IP_E_DEVICE_ASSERT = -7
 IP_E_STATE = -8
 
-PAGERANK, HASHMIN, SSSP = 0, 1, 2
-APPS = {"pagerank": PAGERANK, "hashmin": HASHMIN, "sssp": SSSP}
+PAGERANK, HASHMIN, SSSP, RELIABILITY = 0, 1, 2, 3
+APPS = {"pagerank": PAGERANK, "hashmin": HASHMIN, "sssp": SSSP, "reliability": RELIABILITY}
+FLOAT_APPS = ("pagerank", "reliability")
 PUSH_SPARSE, PUSH_DENSE, PULL = 0, 1, 2
 MODES = {"push_sparse": PUSH_SPARSE, "push_dense": PUSH_DENSE, "pull": PULL}
 PR_ENGINES = {"auto": 0, "gather": 1, "blocked": 2}
@@ -357,7 +358,8 @@ class Graph:
         L = load()
         st = _stream_handle(stream)
         if out is None:
-            dt = np.float32 if app == "pagerank" or app == PAGERANK else np.uint32
+            name = app if isinstance(app, str) or app is None else {v: k for k, v in APPS.items()}[int(app)]
+            dt = np.float32 if name in FLOAT_APPS else np.uint32
             out = np.empty(self.n, dt)
         if _is_torch(out):
             _check(L.ip_get_values(self._h, out.data_ptr(), out.numel() * out.element_size(), int(out.is_cuda), st),

@@ -964,7 +964,7 @@ int ip_set_selector(ip_graph_t* g, const void* blob, size_t bytes) {
 
 int ip_run(ip_graph_t* g, ip_app_t app, uint32_t max_supersteps, const ip_options_t* opt, ip_run_stats_t* stats) {
     if (!g) return IP_E_INVAL;
-    if (app != IP_PAGERANK && app != IP_HASHMIN && app != IP_SSSP) return IP_E_INVAL;
+    if (app != IP_PAGERANK && !ipg::program_ops((int)app)) return IP_E_INVAL;  // a registered vertex program
     if (max_supersteps == 0) return IP_E_INVAL;
     return run_app(g, (int)app, max_supersteps, opt, stats);
 }

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/ipregel.h"
+#include "../../include/ipregel_program.cuh"
 
 namespace ipg {
 
@@ -149,15 +150,29 @@ struct Params {
     const uint32_t* orig;  // renumbered graph: internal id -> caller's id (Hashmin labels are caller ids), else null
 };
 
+// PageRank (Fig. 8) in the terms of the vertex-program interface: a sum combiner
+// (FP32, atomicAdd in the push exchange), compute() forming the rank from the
+// combined sum, and the broadcast rank / out-degree. Every vertex is active for T
+// supersteps, so PageRank runs in its own engines (the CSC gather and the blocked
+// pull below, the push in superstep.cu), which all take these three pieces.
+struct PageRankProgram {
+    using Combiner = ipregel::SumCombiner<float>;
+    using Value = float;
+    // (1-d)/N + d * sum, with base = (1-d)/N rounded to FP32
+    __device__ static float compute(float damping, float base, float sum) { return fmaf(damping, sum, base); }
+    // the message of a vertex that broadcasts: rank / out-degree (0 for a vertex without out-edges)
+    __device__ static float message(float rank, float inv_outdeg) { return rank * inv_outdeg; }
+};
+
 // PageRank compute() of superstep s (Fig. 8): rank from the sum of the received
 // broadcasts, then broadcast rank / out-degree while s < T. With a tolerance, the
 // rank's change is added to the calling thread's L1 partial dacc.
 __device__ __forceinline__ void pr_finish(const Params& P, uint32_t v, float sum, uint32_t s, float* nxt,
                                           float& dacc) {
-    const float r = fmaf(P.damping, sum, P.pr_base);  // (1-d)/N + d * sum
+    const float r = PageRankProgram::compute(P.damping, P.pr_base, sum);
     if (P.pr_tol > 0.f) dacc += fabsf(r - P.rank[v]);
     P.rank[v] = r;
-    nxt[v] = s < P.T ? r * P.inv_outdeg[v] : 0.0f;
+    nxt[v] = s < P.T ? PageRankProgram::message(r, P.inv_outdeg[v]) : 0.0f;
 }
 
 // Adds the calling warp's L1 partials to the superstep's rank change (all 32 lanes
@@ -259,6 +274,8 @@ void pb_free(ip_graph* g);
 size_t pb_bytes(const ip_graph* g);  // device bytes of the blocked layout (0 if not built)
 int unpermute(const ip_graph* g, const uint32_t* in, uint32_t* out, cudaStream_t st);
 // superstep.cu
+struct ProgramOps;
+const ProgramOps* program_ops(int app);  // the vertex program registered as app, or null
 int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* opt, ip_run_stats_t* stats);
 void free_graph_exec(ip_graph* g);
 }  // namespace ipg

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(PB1_THREADS) k_pb_scatter(Params P) {
                 iod[u] = i < ns ? __ldg(P.inv_outdeg + s0 + i) : 0.0f;
             }
 #pragma unroll
-            for (int u = 0; u < PB_BATCH; ++u) x[u] = sent ? x[u] * iod[u] : 0.0f;  // as pr_finish
+            for (int u = 0; u < PB_BATCH; ++u) x[u] = sent ? PageRankProgram::message(x[u], iod[u]) : 0.0f;
 #pragma unroll
             for (int u = 0; u < PB_BATCH; ++u) {
                 const uint32_t i = i0 + u * blockDim.x;
@@ -262,7 +262,7 @@ __device__ __forceinline__ void pb_finish(const Params& P, uint32_t* hi, uint32_
             h = __ldcg(hi + v);
             if (h) hi[v] = 0;
         }
-        const float r = fmaf(P.damping, pb_value(h, lo[v], inv_scale), P.pr_base);  // as pr_finish
+        const float r = PageRankProgram::compute(P.damping, P.pr_base, pb_value(h, lo[v], inv_scale));
         if (P.pr_tol > 0.f) dacc += fabsf(r - P.rank[v0 + v]);  // tolerance runs only
         P.rank[v0 + v] = r;
         lo[v] = 0;
