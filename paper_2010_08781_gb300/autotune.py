@@ -42,33 +42,38 @@ def time_run(G, app, reps, **kw):
     return statistics.median(ts)
 
 
-def tune_bins(reps=3, relabel=True, log=print):
-    """Grid search of (t1, t2) per app; total time over the tuning graphs, stored
-    renumbered by degree class (relabel=True) or in the caller's order."""
+def tune_bins(reps=3, relabel=True, log=print, graphs=None, t1s=T1S, t2s=T2S):
+    """Grid search of (t1, t2) per app; total time over the tuning graphs (name,
+    inputs.Graph pairs; a name ending in "d" marks a directed graph, tuned for
+    PageRank), stored renumbered by degree class (relabel=True) or in the caller's
+    order."""
     totals = {app: {} for app in ("hashmin", "sssp", "pagerank")}
-    for name, g in _graphs():
+    for name, g in (graphs if graphs is not None else _graphs()):
         with Graph.from_inputs(g, relabel=relabel) as G:
             apps = ("pagerank",) if name.endswith("d") else ("hashmin", "sssp")
             for app in apps:
                 # the degree bins schedule the CSC gather engine (the blocked engine has its own layout)
                 kw = dict(policy="forced", forced_mode="pull", pr_engine="gather") if app == "pagerank" else {}
-                for t1 in T1S:
-                    for t2 in T2S:
+                for t1 in t1s:
+                    for t2 in t2s:
                         G.run(app, t1=t1, t2=t2, **kw)  # warm-up (bins rebuilt for the new cutoffs)
                         ms = time_run(G, app, reps, t1=t1, t2=t2, **kw)
                         totals[app][(t1, t2)] = totals[app].get((t1, t2), 0.0) + ms
             log(f"tuned bins on {name}")
     best = {}
     for app, d in totals.items():
+        if not d:
+            continue
         (t1, t2), ms = min(d.items(), key=lambda kv: kv[1])
         best[app] = {"t1": t1, "t2": t2, "ms": round(ms, 4),
                      "grid_ms": {f"{a},{b}": round(v, 4) for (a, b), v in sorted(d.items())}}
     return best
 
 
-def tune_modes(log=print):
+def tune_modes(log=print, specs=None):
     from . import selector
-    specs = [dict(kind="rmat", scale=s, a=a, seed=5) for s in (20, 22) for a in (0.45, 0.57, 0.65)]
+    if specs is None:
+        specs = [dict(kind="rmat", scale=s, a=a, seed=5) for s in (20, 22) for a in (0.45, 0.57, 0.65)]
     X, T, _ = selector.collect_many(specs, log=log)
     a, b = selector.tune_threshold(X, T)
     return {"thr_sparse": a, "thr_pull": b, "samples": int(X.shape[0])}

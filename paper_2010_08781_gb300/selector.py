@@ -12,7 +12,10 @@ packed by ip_mlp_pack into the blob that ip_set_selector loads.
 
 Command line (on a GPU machine):
     python -m paper_2010_08781_gb300.selector train --out DIR
-writes DIR/selector_weights.bin, DIR/selector_report.json and the logs.
+writes DIR/selector_weights.bin, DIR/selector_report.json and the logs;
+    python -m paper_2010_08781_gb300.selector evaluate --out DIR
+times whole runs of the shipped selector against the threshold rule on the
+held-out graphs of held_out_graphs() (DIR/selector_held_out.json).
 """
 from __future__ import annotations
 
@@ -190,7 +193,8 @@ def make_graph(spec):
         return inputs.er_graph(n, 8 * n, seed=spec["seed"], symmetrize=True, weighted=True)
     a = spec["a"]
     b = c = (1.0 - a - 0.05) / 2
-    return inputs.rmat_graph(spec["scale"], 16, a, b, c, seed=spec["seed"], symmetrize=True, weighted=True)
+    return inputs.rmat_graph(spec["scale"], 16, a, b, c, seed=spec["seed"], symmetrize=True, weighted=True,
+                             permute_seed=spec.get("permute"))
 
 
 def collect_many(specs, sssp_sources=4, log=print):
@@ -239,9 +243,57 @@ def live_compare(specs, blob, thr_sparse, thr_pull, reps=5):
     return out
 
 
+def held_out_graphs():
+    """A wider held-out set than evaluation_graphs (no seed of any training graph,
+    several shapes): R-MAT 22 like the benchmark's secondary line but other seeds,
+    R-MAT 23 with a = .45 and .65, R-MAT 24 (a = .57), Erdos-Renyi at 2^22 and 2^24
+    vertices, and a randomly permuted R-MAT 22."""
+    specs = [dict(kind="rmat", scale=22, a=0.57, seed=s) for s in (11, 12)]
+    specs += [dict(kind="rmat", scale=23, a=a, seed=11) for a in (0.45, 0.65)]
+    specs += [dict(kind="rmat", scale=24, a=0.57, seed=s) for s in (11, 12)]
+    specs += [dict(kind="er", scale=22, a=None, seed=11), dict(kind="er", scale=24, a=None, seed=11)]
+    specs += [dict(kind="rmat", scale=22, a=0.57, seed=13, permute=17)]
+    return specs
+
+
+def evaluate_live(specs, reps=7, sources=3, log=print):
+    """Whole runs of both apps in the device-driven loop, learned selector against
+    the threshold rule (the engine's defaults): the two policies alternate run by
+    run (so drift hits both alike); median ms per (graph, app, source)."""
+    import inputs
+    rows = []
+    for spec in specs:
+        g = make_graph(spec)
+        with Graph.from_inputs(g) as G:
+            runs = [("hashmin", 0)] + [("sssp", int(x)) for x in
+                                       [0] + inputs.uniform_vertices(g.n, sources - 1, seed=spec["seed"] + 29).tolist()]
+            for app, src in runs:
+                kw = dict(source=src) if app == "sssp" else {}
+                ts = {"mlp": [], "threshold": []}
+                for _ in range(reps):
+                    for pol in ("mlp", "threshold"):
+                        ts[pol].append(G.run(app, policy=pol, **kw).elapsed_ms)
+                row = dict(spec, app=app, source=src, edges=g.m,
+                           mlp_ms=round(float(np.median(ts["mlp"])), 4),
+                           threshold_ms=round(float(np.median(ts["threshold"])), 4))
+                row["gain"] = round(row["threshold_ms"] / row["mlp_ms"] - 1.0, 4)
+                rows.append(row)
+                log(json.dumps(row))
+        del g
+    summary = {}
+    for app in ("hashmin", "sssp"):
+        r = [x for x in rows if x["app"] == app]
+        tot_m, tot_t = sum(x["mlp_ms"] for x in r), sum(x["threshold_ms"] for x in r)
+        summary[app] = {"runs": len(r), "mlp_ms": round(tot_m, 3), "threshold_ms": round(tot_t, 3),
+                        "gain_total_time": round(tot_t / tot_m - 1.0, 4),
+                        "gain_geomean": round(float(np.exp(np.mean([np.log(1 + x["gain"]) for x in r]))) - 1.0, 4),
+                        "runs_won": int(sum(x["gain"] > 0 for x in r))}
+    return rows, summary
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["train"])
+    ap.add_argument("cmd", choices=["train", "evaluate"])
     ap.add_argument("--out", default=".")
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--lr", type=float, default=3e-3)
@@ -249,6 +301,12 @@ def main():
                     help="feature indices the network ignores (e.g. 5: the last superstep's time)")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
+    if args.cmd == "evaluate":
+        rows, summary = evaluate_live(held_out_graphs())
+        with open(os.path.join(args.out, "selector_held_out.json"), "w") as f:
+            json.dump({"graphs": held_out_graphs(), "runs": rows, "summary": summary}, f, indent=1)
+        print(json.dumps(summary))
+        return
     Xtr, Ttr, meta_tr = collect_many(training_graphs())
     Xev, Tev, meta_ev = collect_many(evaluation_graphs())
     np.savez_compressed(os.path.join(args.out, "selector_logs.npz"), Xtr=Xtr, Ttr=Ttr, Xev=Xev, Tev=Tev)
