@@ -13,7 +13,8 @@ leg, and by nothing else. The GPU product path never imports this package.
   from the ranks of the superstep before (FP64 numpy): checks a single superstep
   of a run too large for the full oracle, one vertex at a time.
   ``pagerank_superstep`` is the same update for a range of vertices in C, used
-  to check and to time one superstep of a billion-edge graph.
+  to check and to time one superstep of a billion-edge graph;
+  ``hashmin_superstep`` is one Hashmin superstep (Fig. 9) in the same form.
 * PageRank to convergence (``pagerank(..., tolerance=eps)``): the run ends after
   the first superstep whose L1 rank change is below eps.
 * ``reliability`` — the most reliable path (an application the paper does not
@@ -72,6 +73,10 @@ def _L():
             lib.oracle_pagerank_superstep.argtypes = [ctypes.c_uint32, U32, U32, U32, F64, ctypes.c_double,
                                                       ctypes.c_uint32, ctypes.c_uint32, F64]
             lib.oracle_pagerank_superstep.restype = None
+            U8 = ctypes.POINTER(ctypes.c_uint8)
+            lib.oracle_hashmin_superstep.argtypes = [ctypes.c_uint32, U32, U32, U32, U8, ctypes.c_uint32,
+                                                     ctypes.c_uint32, U32, U8]
+            lib.oracle_hashmin_superstep.restype = None
             lib.oracle_hashmin.argtypes = [ctypes.c_uint32, U32, U32, ctypes.c_uint32, U32, st]
             lib.oracle_sssp.argtypes = [ctypes.c_uint32, U32, U32, U32, ctypes.c_uint32, ctypes.c_uint32, U32, st]
             lib.oracle_reliability.argtypes = [ctypes.c_uint32, U32, U32, U32, ctypes.c_uint32, ctypes.c_uint32,
@@ -140,6 +145,24 @@ def pagerank_superstep(n, in_ptr, in_src, out_degree, prev_rank, damping=0.85, v
                                    prev.ctypes.data_as(F64), float(damping), int(v_begin), int(v_end),
                                    out.ctypes.data_as(F64))
     return out[:v_end - v_begin]
+
+
+def hashmin_superstep(n, in_ptr, in_src, prev_label, bcast, v_begin=0, v_end=None, with_recv=False):
+    """One superstep s >= 1 of Hashmin (Fig. 9) for the vertices [v_begin, v_end),
+    in C, from the receiving side: bcast[u] (uint8) marks the vertices that broadcast
+    prev_label[u] in superstep s-1. Returns the new labels (and, with with_recv,
+    which vertices received a message)."""
+    v_end = n if v_end is None else v_end
+    ip, isrc, pl = _u32(in_ptr), _u32(in_src), _u32(prev_label)
+    bc = np.ascontiguousarray(bcast, dtype=np.uint8)
+    out = np.empty(max(v_end - v_begin, 1), np.uint32)
+    rc = np.empty(max(v_end - v_begin, 1), np.uint8)
+    U8 = ctypes.POINTER(ctypes.c_uint8)
+    _L().oracle_hashmin_superstep(n, ip.ctypes.data_as(U32), isrc.ctypes.data_as(U32), pl.ctypes.data_as(U32),
+                                  bc.ctypes.data_as(U8), int(v_begin), int(v_end), out.ctypes.data_as(U32),
+                                  rc.ctypes.data_as(U8))
+    k = v_end - v_begin
+    return (out[:k], rc[:k].astype(bool)) if with_recv else out[:k]
 
 
 def hashmin(n, row_ptr, col, max_supersteps=1 << 30, stats_cap=4096):

@@ -457,3 +457,28 @@ int oracle_reliability(uint32_t n, const uint32_t* row_ptr, const uint32_t* col,
     teardown(&e);
     return r;
 }
+
+/* One superstep s >= 1 of Hashmin (Fig. 9) for the vertices [v_begin, v_end),
+ * written from the receiving side: the in-neighbours u of v with bcast[u] != 0
+ * broadcast prev_label[u] in superstep s-1, the min combiner folded them, and
+ * compute() keeps the smaller of the vertex's label and that minimum.
+ * out_label[v - v_begin] receives the new label; out_recv[v - v_begin] (may be
+ * NULL) whether v received a message (and so ran compute()). Used to time a
+ * bounded sample of a Hashmin run and to check single supersteps. */
+void oracle_hashmin_superstep(uint32_t n, const uint32_t* in_ptr, const uint32_t* in_src, const uint32_t* prev_label,
+                              const uint8_t* bcast, uint32_t v_begin, uint32_t v_end, uint32_t* out_label,
+                              uint8_t* out_recv) {
+    (void)n;
+    for (uint32_t v = v_begin; v < v_end; ++v) {
+        uint32_t m = ORACLE_INF;
+        int got = 0;
+        for (uint32_t k = in_ptr[v]; k < in_ptr[v + 1]; ++k) {
+            const uint32_t u = in_src[k];
+            if (!bcast[u]) continue;
+            got = 1;
+            if (prev_label[u] < m) m = prev_label[u];
+        }
+        out_label[v - v_begin] = (got && m < prev_label[v]) ? m : prev_label[v];
+        if (out_recv) out_recv[v - v_begin] = (uint8_t)got;
+    }
+}

@@ -550,3 +550,34 @@ def test_reliability_unit_weights_are_bfs_layers():
     assert (got[~reach] == 0).all()
     layers = np.bincount(depth[reach].astype(int))
     assert st["broadcasters"][:len(layers)].tolist() == layers.tolist()
+
+
+# ------------------------------------------------- Hashmin, one superstep in C
+@pytest.mark.parametrize("sym", [True, False])
+def test_hashmin_superstep_iterated_is_the_engine(sym):
+    """Pull-form supersteps of Hashmin, each vertex broadcasting when its label
+    dropped in the superstep before (all of them in superstep 0), reproduce the push
+    engine: the labels after every superstep, the recipients (active vertices) and
+    the broadcasters, until no vertex broadcasts; the labels are then the union-find
+    component minima on the symmetrised graph."""
+    g = inputs.rmat_graph(11, symmetrize=sym, seed=6)
+    label = np.arange(g.n, dtype=np.uint32)
+    bcast = np.ones(g.n, np.uint8)
+    _, full = oracle.hashmin(g.n, g.row_ptr, g.col)
+    s = 0
+    while bcast.any():
+        s += 1
+        new, recv = oracle.hashmin_superstep(g.n, g.t_ptr, g.t_idx, label, bcast, with_recv=True)
+        got_s, st = oracle.hashmin(g.n, g.row_ptr, g.col, max_supersteps=s + 1)
+        assert np.array_equal(new, got_s), s
+        assert int(recv.sum()) == int(full["active"][s])
+        bcast = ((new < label) & (g.out_degree() > 0)).astype(np.uint8)
+        assert int((new < label).sum()) == int(full["broadcasters"][s])
+        label = new
+    assert s + 1 == full["supersteps"]
+    if sym:
+        from scipy.sparse.csgraph import connected_components
+        _, comp = connected_components(_csr_matrix(g), directed=False)
+        mins = np.full(comp.max() + 1, g.n, np.int64)
+        np.minimum.at(mins, comp, np.arange(g.n))
+        assert np.array_equal(label, mins[comp])
