@@ -71,7 +71,9 @@ typedef enum { IP_MODE_PUSH_SPARSE = 0, IP_MODE_PUSH_DENSE = 1, IP_MODE_PULL = 2
 typedef enum {
     IP_POLICY_AUTO = 0,      /* the learned selector if one is loaded, else the threshold rule */
     IP_POLICY_THRESHOLD = 1, /* fixed rule on the frontier's out-edge fraction (see ip_options_t) */
-    IP_POLICY_MLP = 2,       /* the learned selector; IP_E_STATE if none is loaded */
+    IP_POLICY_MLP = 2,       /* the learned selector; IP_E_STATE if none is loaded. A superstep whose
+                                frontier sends fewer than thr_sparse * E messages takes PUSH_SPARSE
+                                without running the network (the threshold rule's sparse region) */
     IP_POLICY_FORCED = 3,    /* always forced_mode */
     IP_POLICY_SEQUENCE = 4   /* exchange into superstep s uses mode_sequence[(s-1) % len] */
 } ip_policy_t;
@@ -194,14 +196,21 @@ void ip_options_default(ip_options_t* opt);
  *                device"; csc_offsets == csr_offsets and csc_rows == csr_cols
  *                declares a symmetric graph and shares the arrays. csc_weights
  *                is required when csc arrays and csr_weights are both given.
- *   device_ptrs  0: all arrays are host memory; 1: all are device memory.
+ *   flags        IP_CREATE_DEVICE_PTRS: all arrays are device memory (else all are
+ *                host memory; 0 and 1 keep their old meaning); IP_CREATE_RELABEL:
+ *                renumber the vertices by degree class as part of creation, exactly as
+ *                ip_graph_create followed by ip_graph_relabel, except that the in-edges
+ *                and degree bins are built once, for the renumbered graph. Other bits:
+ *                IP_E_INVAL.
  * Host arrays are validated on the host (IP_E_INVAL / IP_E_RANGE); device
  * arrays by a device check (same codes). The library copies every array.
  * A CSC that is not the transpose of the CSR is not detected: pull mode then
  * computes on the CSC's edges. */
+#define IP_CREATE_DEVICE_PTRS 1
+#define IP_CREATE_RELABEL 2
 int ip_graph_create(ip_graph_t** out, uint32_t n_vertices, uint64_t n_edges, const uint32_t* csr_offsets,
                     const uint32_t* csr_cols, const uint32_t* csr_weights, const uint32_t* csc_offsets,
-                    const uint32_t* csc_rows, const uint32_t* csc_weights, int device_ptrs, void* stream);
+                    const uint32_t* csc_rows, const uint32_t* csc_weights, int flags, void* stream);
 
 /* Releases the graph store and the run state of the handle (the vertex and
  * edge arrays of Section 4.2, the mailboxes of Section 4.3.3 and everything the

@@ -88,6 +88,7 @@ BATCH_MAX_SOURCES = 256
 MLP_PARAMS = 32 * 8 + 32 + 32 * 32 + 32 + 3 * 32 + 3
 NOALLOC_MAX_VERTICES = 1 << 20
 RELABEL_AUTO_EDGES = 1 << 20  # graphs this large are renumbered by degree class unless asked otherwise
+CREATE_DEVICE_PTRS, CREATE_RELABEL = 1, 2
 
 
 def lib_path() -> str:
@@ -273,13 +274,12 @@ class Graph:
         self.n = int(n)
         self.m = m
         st = _stream_handle(stream)
-        _check(L.ip_graph_create(ctypes.byref(self._h), self.n, m, *p, device_ptrs, st), "ip_graph_create")
-        self._keep = None  # the library copied everything
-        self.relabeled = False
         if relabel == "auto":
             relabel = m >= RELABEL_AUTO_EDGES
-        if relabel:
-            self.relabel(stream)
+        flags = device_ptrs | (CREATE_RELABEL if relabel else 0)  # renumbered during creation
+        _check(L.ip_graph_create(ctypes.byref(self._h), self.n, m, *p, flags, st), "ip_graph_create")
+        self._keep = None  # the library copied everything
+        self.relabeled = bool(relabel)
         if selector == "default":
             from .selector import load_default_blob
             selector = load_default_blob()

@@ -241,24 +241,75 @@ static int exclusive_scan(ip_graph* g, uint32_t* data, uint64_t n, cudaStream_t 
     return r;
 }
 
-// Transposition scatter: edge e = (u, v) goes to a free slot of v's in-list.
-// Slot order inside an in-list follows atomic arrival order.
-__global__ void k_scatter_in(const uint32_t* csr_off, const uint32_t* col, const uint32_t* w, uint32_t n, uint64_t E,
-                             uint32_t* cursor, uint32_t* row, uint32_t* wt) {
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E; e += (uint64_t)gridDim.x * blockDim.x) {
-        // source u: the last u with csr_off[u] <= e
-        uint32_t lo = 0, hi = n;  // invariant: csr_off[lo] <= e < csr_off[hi]
+// Edge chunks for the warp-per-chunk edge kernels (transposition, renumbering copy).
+constexpr uint32_t RL_CH = 1024;
+constexpr uint32_t RL_UNROLL = 4;
+
+// chunk_src[c] = the source of edge position c * RL_CH (largest s with off[s] <= c * RL_CH).
+__global__ void k_rl_chunk_src(const uint32_t* __restrict__ off_new, uint32_t n, uint32_t n_chunks,
+                               uint32_t* chunk_src) {
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_chunks; c += gridDim.x * blockDim.x) {
+        const uint64_t p = (uint64_t)c * RL_CH;
+        uint32_t lo = 0, hi = n;  // off_new[lo] <= p; the answer is below hi
         while (hi - lo > 1) {
-            uint32_t mid = lo + (hi - lo) / 2;
-            if ((uint64_t)csr_off[mid] <= e)
+            const uint32_t mid = lo + (hi - lo) / 2;
+            if (off_new[mid] <= p)
                 lo = mid;
             else
                 hi = mid;
         }
-        uint32_t v = col[e];
-        uint32_t pos = atomicAdd(&cursor[v], 1u);
-        row[pos] = lo;
-        if (w) wt[pos] = w[e];
+        chunk_src[c] = lo;
+    }
+}
+
+// Transposition scatter: edge e = (u, v) goes to a free slot of v's in-list
+// (slot order inside an in-list follows atomic arrival order). One warp per chunk
+// of RL_CH consecutive edges: the chunk's first source comes from chunk_src, the
+// warp keeps the first edges of 32 consecutive sources in registers and finds each
+// lane's source by a 5-step shuffle search (a source owns edge e when it is the
+// last one starting at or before e), so no edge searches the whole offset array.
+__global__ void k_scatter_in(const uint32_t* __restrict__ csr_off, const uint32_t* __restrict__ chunk_src,
+                             const uint32_t* __restrict__ col, const uint32_t* __restrict__ w, uint32_t n,
+                             uint64_t E, uint32_t n_chunks, uint32_t* cursor, uint32_t* __restrict__ row,
+                             uint32_t* __restrict__ wt) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += nw) {
+        const uint64_t p0 = (uint64_t)c * RL_CH;
+        const uint64_t p1 = p0 + RL_CH < E ? p0 + RL_CH : E;
+        for (uint64_t s = chunk_src[c];; s += 32) {  // windows of 32 sources
+            const uint64_t sl = s + lane;
+            const uint32_t wo = sl < n ? csr_off[sl] : (uint32_t)E;  // the lane's source: its first edge
+            const uint64_t wend = s + 32 <= n ? (uint64_t)csr_off[s + 32] : E;
+            const uint64_t w0 = __shfl_sync(FULL, wo, 0);
+            const uint64_t lo = p0 > w0 ? p0 : w0, hi = p1 < wend ? p1 : wend;
+            for (uint64_t base = lo; base < hi; base += 32 * RL_UNROLL) {
+                uint32_t e[RL_UNROLL], u[RL_UNROLL], v[RL_UNROLL], wv[RL_UNROLL];
+#pragma unroll
+                for (uint32_t k = 0; k < RL_UNROLL; ++k) {
+                    const uint64_t ee = base + 32 * k + lane;
+                    e[k] = ee < hi ? (uint32_t)ee : 0xFFFFFFFFu;
+                    uint32_t i = 0;  // largest i with wo(i) <= e
+#pragma unroll
+                    for (uint32_t step = 16; step; step >>= 1)
+                        if (__shfl_sync(FULL, wo, i + step) <= e[k]) i += step;
+                    u[k] = (uint32_t)(s + i);
+                }
+#pragma unroll
+                for (uint32_t k = 0; k < RL_UNROLL; ++k) {
+                    v[k] = e[k] != 0xFFFFFFFFu ? col[e[k]] : 0u;
+                    wv[k] = (w && e[k] != 0xFFFFFFFFu) ? w[e[k]] : 0u;
+                }
+#pragma unroll
+                for (uint32_t k = 0; k < RL_UNROLL; ++k)
+                    if (e[k] != 0xFFFFFFFFu) {
+                        const uint32_t pos = atomicAdd(&cursor[v[k]], 1u);
+                        row[pos] = u[k];
+                        if (w) wt[pos] = wv[k];
+                    }
+            }
+            if (wend >= p1) break;
+        }
     }
 }
 
@@ -480,23 +531,39 @@ static int transpose_csr(ip_graph* g, cudaStream_t st) {
     }
     if ((r = exclusive_scan(g, g->csc_off, (uint64_t)n + 1, st))) return r;
     uint32_t* cursor = nullptr;
+    uint32_t* chunk_src = nullptr;
+    const uint32_t n_chunks = (uint32_t)((E + RL_CH - 1) / RL_CH);
     if ((r = alloc_dev(g, (void**)&cursor, (size_t)n * sizeof(uint32_t)))) return r;
     g->device_bytes -= (size_t)n * sizeof(uint32_t);
+    if ((r = alloc_dev(g, (void**)&chunk_src, std::max<size_t>(n_chunks, 1) * sizeof(uint32_t)))) {
+        free_dev(cursor);
+        return r;
+    }
+    g->device_bytes -= std::max<size_t>(n_chunks, 1) * sizeof(uint32_t);
     CK(cudaMemcpyAsync(cursor, g->csc_off, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
-    if (E)
-        k_scatter_in<<<grid_for(g, E), 256, 0, st>>>(g->csr_off, g->csr_col, g->csr_w, n, E, cursor, g->csc_row,
-                                                      g->csc_w);
+    if (E) {
+        k_rl_chunk_src<<<grid_for(g, n_chunks), 256, 0, st>>>(g->csr_off, n, n_chunks, chunk_src);
+        k_scatter_in<<<grid_for(g, (uint64_t)n_chunks * 32), 256, 0, st>>>(g->csr_off, chunk_src, g->csr_col, g->csr_w,
+                                                                           n, E, n_chunks, cursor, g->csc_row, g->csc_w);
+    }
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(st);
     free_dev(cursor);
+    free_dev(chunk_src);
     CK(e1);
     CK(e2);
     return IP_OK;
 }
 
+static int relabel(ip_graph* g, cudaStream_t st);
+
 static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, const uint32_t* csr_col,
                   const uint32_t* csr_w, const uint32_t* csc_off, const uint32_t* csc_row, const uint32_t* csc_w,
-                  int device_ptrs, cudaStream_t st) {
+                  int flags, cudaStream_t st) {
+    const int device_ptrs = (flags & IP_CREATE_DEVICE_PTRS) ? 1 : 0;
+    // renumbering as part of creation: the in-edges and degree bins are built once, for
+    // the renumbered graph (a CSC given by the caller is still copied and then rebuilt)
+    const bool renumber = (flags & IP_CREATE_RELABEL) != 0;
     CK(cudaGetDevice(&g->device));
     CK(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
     g->V = n;
@@ -527,10 +594,10 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
         if ((r = upload(g, &g->csc_row, csc_row, E, ea, device_ptrs, st))) return r;
         if (csc_w && (r = upload(g, &g->csc_w, csc_w, E, ea, device_ptrs, st))) return r;
         if ((r = validate_device(g, g->csc_off, g->csc_row, st))) return r;
-    } else if ((r = transpose_csr(g, st))) {
+    } else if (!renumber && (r = transpose_csr(g, st))) {
         return r;
     }
-    if (csr_w && !g->csc_w) return IP_E_INVAL;
+    if (csr_w && !g->csc_w && !(renumber && !csc_off)) return IP_E_INVAL;
 
     // per-vertex arrays
     const size_t nv = (size_t)n;
@@ -560,17 +627,21 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
     CK(cudaMemcpyAsync(&g->max_out_deg, mx, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaMemsetAsync(mx, 0, 4, st));
-    k_degrees<<<grid_for(g, n), 256, 0, st>>>(g->csc_off, n, nullptr, mx);
+    if ((r = alloc_dev(g, (void**)&g->hq[0], sizeof(uint2)))) return r;
+    if ((r = alloc_dev(g, (void**)&g->hq[1], sizeof(uint2)))) return r;
+    g->hq_cap = 0;
+    CK(cudaEventCreate(&g->ev0));
+    CK(cudaEventCreate(&g->ev1));
+    if (renumber) {
+        if ((r = relabel(g, st))) return r;  // transposes (directed) and builds the bins
+    } else {
+        if ((r = ensure_bins(g, DEFAULT_T1, DEFAULT_T2, st))) return r;
+    }
+    k_degrees<<<grid_for(g, n), 256, 0, st>>>(g->csc_off, n, nullptr, mx);  // max in-degree
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&g->max_in_deg, mx, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaMemsetAsync(mx, 0, 4, st));
-    if ((r = alloc_dev(g, (void**)&g->hq[0], sizeof(uint2)))) return r;
-    if ((r = alloc_dev(g, (void**)&g->hq[1], sizeof(uint2)))) return r;
-    g->hq_cap = 0;
-    if ((r = ensure_bins(g, DEFAULT_T1, DEFAULT_T2, st))) return r;
-    CK(cudaEventCreate(&g->ev0));
-    CK(cudaEventCreate(&g->ev1));
     CK(cudaStreamSynchronize(st));
     return IP_OK;
 }
@@ -632,26 +703,6 @@ __global__ void k_rl_place(const uint32_t* __restrict__ off, uint32_t n, uint32_
 // the first new and old edge positions of 32 consecutive sources in registers, and
 // each lane finds the source of its edge by a binary search over them (shuffles).
 // Writes are coalesced whatever the degrees; the targets are renumbered on the way.
-constexpr uint32_t RL_CH = 1024;
-constexpr uint32_t RL_UNROLL = 4;
-
-// chunk_src[c] = the source of new edge position c * RL_CH (largest s with off_new[s] <= c * RL_CH).
-__global__ void k_rl_chunk_src(const uint32_t* __restrict__ off_new, uint32_t n, uint32_t n_chunks,
-                               uint32_t* chunk_src) {
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_chunks; c += gridDim.x * blockDim.x) {
-        const uint64_t p = (uint64_t)c * RL_CH;
-        uint32_t lo = 0, hi = n;  // off_new[lo] <= p; the answer is below hi
-        while (hi - lo > 1) {
-            const uint32_t mid = lo + (hi - lo) / 2;
-            if (off_new[mid] <= p)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        chunk_src[c] = lo;
-    }
-}
-
 __global__ void k_rl_edges(const uint32_t* __restrict__ off_new, const uint32_t* __restrict__ start_old,
                            const uint32_t* __restrict__ chunk_src, const uint32_t* __restrict__ col,
                            const uint32_t* __restrict__ w, const uint32_t* __restrict__ new_of_old, uint32_t n,
@@ -769,7 +820,7 @@ static int relabel(ip_graph* g, cudaStream_t st) {
         free_dev(start_old);
         free_dev(chunk_src);
         g->device_bytes -= (size_t)nblk * RL_KEYS * 8 + (size_t)n * 4 + (size_t)n_chunks * 4;
-        if (!alias) {
+        if (!alias && g->csc_off) {  // (creation with renumbering may not have built it yet)
             free_dev(g->csc_off);
             free_dev(g->csc_row);
             free_dev(g->csc_w);
@@ -877,9 +928,10 @@ int ip_release_cached_memory(void) {
 
 int ip_graph_create(ip_graph_t** out, uint32_t n_vertices, uint64_t n_edges, const uint32_t* csr_offsets,
                     const uint32_t* csr_cols, const uint32_t* csr_weights, const uint32_t* csc_offsets,
-                    const uint32_t* csc_rows, const uint32_t* csc_weights, int device_ptrs, void* stream) {
+                    const uint32_t* csc_rows, const uint32_t* csc_weights, int flags, void* stream) {
     if (!out) return IP_E_INVAL;
     *out = nullptr;
+    if (flags & ~(IP_CREATE_DEVICE_PTRS | IP_CREATE_RELABEL)) return IP_E_INVAL;
     if (n_vertices == 0 || n_vertices == 0xFFFFFFFFu || !csr_offsets) return IP_E_INVAL;
     if (n_edges >= 0xFFFFFFFFull) return IP_E_RANGE;
     if (n_edges > 0 && !csr_cols) return IP_E_INVAL;
@@ -890,7 +942,7 @@ int ip_graph_create(ip_graph_t** out, uint32_t n_vertices, uint64_t n_edges, con
     ip_graph* g = new (std::nothrow) ip_graph();
     if (!g) return IP_E_NOMEM;
     int r = create(g, n_vertices, n_edges, csr_offsets, csr_cols, csr_weights, csc_offsets, csc_rows,
-                   csr_weights ? csc_weights : nullptr, device_ptrs, (cudaStream_t)stream);
+                   csr_weights ? csc_weights : nullptr, flags, (cudaStream_t)stream);
     if (r != IP_OK) {
         cudaStreamSynchronize((cudaStream_t)stream);
         (void)cudaGetLastError();

@@ -29,6 +29,7 @@
 // runs the CTA chunks first, then the warp vertices, then the tiles. Edge
 // arrays are read as aligned 16-byte blocks, U blocks in flight per thread.
 #include <math.h>
+#include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -234,25 +235,49 @@ __global__ void __launch_bounds__(BLOCK) k_pr_apply(Params P) {
 // ================================================================ selector
 __device__ __forceinline__ float bf16f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
-// One warp: 8 -> 32 -> 32 -> 3 MLP, BF16 weights, FP32 accumulation.
+// One warp: 8 -> 32 -> 32 -> 3 MLP, BF16 weights, FP32 accumulation. Lane j owns
+// hidden unit j of both layers. All of a lane's parameters are loaded at once at
+// the start (its W1 row as one 16-byte load, its W2 row as four, its W3 column,
+// biases, and the feature normalisation by lanes 0-7), so inference waits for one
+// L2 round trip instead of one per layer; the arithmetic and its order are those
+// of the training forward pass (ip_mlp_forward), so the logits are identical.
+static_assert(offsetof(SelectorDev, W1) % 16 == 0 && offsetof(SelectorDev, W2) % 16 == 0, "16-byte weight rows");
 __device__ int mlp_mode(const SelectorDev* S, const float* f) {
     const uint32_t j = lane_id();
+    const uint4 w1 = __ldg(reinterpret_cast<const uint4*>(S->W1) + j);  // W1[j][0..7]
+    uint4 w2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w2[q] = __ldg(reinterpret_cast<const uint4*>(S->W2 + j * 32) + q);  // W2[j][8q..8q+7]
+    const float b1 = __ldg(S->b1 + j), b2 = __ldg(S->b2 + j);
+    uint16_t w3[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) w3[m] = __ldg(S->W3 + m * 32 + j);
+    const float b3m = j < 3 ? __ldg(S->b3 + j) : 0.f;
+    const float mu = j < 8 ? __ldg(S->mu + j) : 0.f, sd = j < 8 ? __ldg(S->sd + j) : 1.f;
     float xn[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) xn[i] = (f[i] - S->mu[i]) / S->sd[i];
-    float h1 = S->b1[j];
+    for (int i = 0; i < 8; ++i) xn[i] = (f[i] - __shfl_sync(FULL, mu, i)) / __shfl_sync(FULL, sd, i);
+    auto lo = [](uint32_t w) { return __uint_as_float(w << 16); };          // element 2t of a pair
+    auto hi = [](uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); };  // element 2t + 1
+    const uint32_t r1[4] = {w1.x, w1.y, w1.z, w1.w};
+    float h1 = b1;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) h1 = fmaf(bf16f(S->W1[j * 8 + i]), xn[i], h1);
+    for (int i = 0; i < 8; ++i) h1 = fmaf((i & 1) ? hi(r1[i >> 1]) : lo(r1[i >> 1]), xn[i], h1);
     h1 = fmaxf(h1, 0.f);
-    float h2 = S->b2[j];
-    for (int k = 0; k < 32; ++k) h2 = fmaf(bf16f(S->W2[j * 32 + k]), __shfl_sync(FULL, h1, k), h2);
+    float h2 = b2;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const uint4 q = w2[k >> 3];
+        const uint32_t pair = (k & 7) < 2 ? q.x : (k & 7) < 4 ? q.y : (k & 7) < 6 ? q.z : q.w;
+        h2 = fmaf((k & 1) ? hi(pair) : lo(pair), __shfl_sync(FULL, h1, k), h2);
+    }
     h2 = fmaxf(h2, 0.f);
     float z[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        float p = bf16f(S->W3[m * 32 + j]) * h2;
+        float p = bf16f(w3[m]) * h2;
         for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
-        z[m] = p + S->b3[m];
+        z[m] = p + __shfl_sync(FULL, b3m, m);
     }
     int best = 0;
     if (z[1] > z[best]) best = 1;
@@ -303,7 +328,9 @@ __global__ void k_select(Params P) {
     switch (P.policy) {
         case IP_POLICY_FORCED: mode = P.forced_mode; break;
         case IP_POLICY_SEQUENCE: mode = P.seq[s % P.seq_len]; break;
-        case IP_POLICY_MLP: mode = mlp_mode(P.sel, f); break;
+        case IP_POLICY_MLP:  // below the sparse cutoff every policy takes push-sparse: no inference there
+            mode = f[6] < P.thr_sparse ? IP_MODE_PUSH_SPARSE : mlp_mode(P.sel, f);
+            break;
         default:
             mode = f[6] < P.thr_sparse ? IP_MODE_PUSH_SPARSE : (f[6] >= P.thr_pull ? IP_MODE_PULL : IP_MODE_PUSH_DENSE);
     }

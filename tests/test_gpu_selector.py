@@ -128,10 +128,11 @@ def test_engine_inference_equals_training_forward():
     with ipg.Graph.from_inputs(g) as G:
         G.set_selector(blob)
         for app in ("hashmin", "sssp"):
-            st = G.run(app, policy="mlp")
-            feats = st.features[: st.supersteps - 1]
-            want = tr.logits(feats).argmax(axis=1)
-            assert st.mode[1:].tolist() == want.tolist()
+            for thr in (0.0, 1e-3):  # below thr_sparse the engine takes push-sparse without inference
+                st = G.run(app, policy="mlp", thr_sparse=thr, thr_pull=max(thr, 0.1))
+                feats = st.features[: st.supersteps - 1]
+                want = np.where(feats[:, 6] < np.float32(thr), 0, tr.logits(feats).argmax(axis=1))
+                assert st.mode[1:].tolist() == want.tolist()
 
 
 def test_trained_selector_gain_on_held_out_graph():
