@@ -78,10 +78,14 @@ typedef enum {
     IP_POLICY_SEQUENCE = 4   /* exchange into superstep s uses mode_sequence[(s-1) % len] */
 } ip_policy_t;
 
-/* How PageRank runs a PULL exchange. Both compute the same sums; they differ in
- * how the in-neighbours' broadcasts reach the destination. */
+/* How a PULL exchange runs, for PageRank and for the vertex programs that allow
+ * the blocked layout (Hashmin). Both engines compute the same combined messages;
+ * they differ in how the in-neighbours' broadcasts reach the destination. */
 typedef enum {
-    IP_PR_ENGINE_AUTO = 0,    /* BLOCKED on graphs of at least 2^24 edges that it supports, else GATHER */
+    IP_PR_ENGINE_AUTO = 0,    /* PageRank: BLOCKED on graphs of at least 2^24 edges that it supports,
+                                 else GATHER. Hashmin: GATHER until the handle has run 10 gather pulls
+                                 (the layout costs about as much to build), BLOCKED from then on (or
+                                 whenever the layout already exists) on graphs of at least 2^24 edges */
     IP_PR_ENGINE_GATHER = 1,  /* every in-edge of the CSC reads its source's broadcast */
     IP_PR_ENGINE_BLOCKED = 2  /* two streaming passes over a second edge layout built on first use
                                  (8 bytes per edge): the sources' broadcasts are written out per
@@ -115,7 +119,8 @@ typedef struct {
     int32_t profile_kernels;      /* 1: host loop with CUDA events around every kernel; fills
                                      ip_run_stats_t.kernel_ms. Values are unchanged. */
     void* stream;                 /* cudaStream_t */
-    int32_t pr_engine;            /* ip_pr_engine_t (default IP_PR_ENGINE_AUTO) */
+    int32_t pr_engine;            /* ip_pr_engine_t: the PULL engine of PageRank and Hashmin
+                                     (default IP_PR_ENGINE_AUTO) */
     float pr_tolerance;           /* PageRank to convergence (the paper's Section 6.1 notes that a
                                      real PageRank runs until convergence): > 0 ends the run after
                                      the first superstep s >= 1 whose L1 rank change

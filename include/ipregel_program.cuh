@@ -18,6 +18,10 @@
  *     static constexpr bool kEarlyExitUnweighted = ...;   // on an unweighted graph every message
  *                                                         // into a superstep is the same (a pull may
  *                                                         // stop at the first one)
+ *     static constexpr bool kBlockedMinPull = ...;        // Combiner is MinCombiner<uint32_t>, message()
+ *                                                         // returns the value unchanged and never the
+ *                                                         // all-ones pattern: the pull may stream the
+ *                                                         // blocked edge layout (Hashmin)
  *     // superstep 0 (the first superstep, Section 4.3.1 condition 1): set the initial
  *     // value and return whether the vertex broadcasts it (caller_id: the vertex's id
  *     // in the caller's numbering; source: ip_options_t.source in the internal one)

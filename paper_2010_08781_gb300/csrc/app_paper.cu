@@ -12,6 +12,7 @@ struct HashminProgram {
     static constexpr bool kAllBroadcastAtStart = true;
     static constexpr bool kUsesSource = false;
     static constexpr bool kEarlyExitUnweighted = false;
+    static constexpr bool kBlockedMinPull = true;  // message = value, labels < 2^32 - 1
     __device__ static bool init(uint32_t, uint32_t caller_id, uint32_t, Value& value) {
         value = caller_id;
         return true;
@@ -38,6 +39,7 @@ struct SsspProgram {
     static constexpr bool kAllBroadcastAtStart = false;
     static constexpr bool kUsesSource = true;
     static constexpr bool kEarlyExitUnweighted = true;
+    static constexpr bool kBlockedMinPull = false;  // the message reads the edge weight
     __device__ static bool init(uint32_t v, uint32_t, uint32_t source, Value& value) {
         value = v == source ? 0u : 0xFFFFFFFFu;
         return v == source;

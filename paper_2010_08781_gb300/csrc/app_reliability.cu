@@ -15,6 +15,7 @@ struct ReliabilityProgram {
     static constexpr bool kAllBroadcastAtStart = false;
     static constexpr bool kUsesSource = true;
     static constexpr bool kEarlyExitUnweighted = false;
+    static constexpr bool kBlockedMinPull = false;
     // superstep 0: the source is certain (1) and broadcasts; every other vertex 0
     __device__ static bool init(uint32_t v, uint32_t, uint32_t source, Value& value) {
         value = v == source ? 1.0f : 0.0f;

@@ -34,6 +34,7 @@ struct ProgramOps {
     const char* name;
     bool uses_source;       // reads ip_options_t.source (range-checked, mapped when renumbered)
     bool float_values;      // values are FP32 (ip_get_values returns floats)
+    bool blocked_min_pull;  // the pull may run on the blocked layout (pb.cu)
     int (*prepare)(const ip_graph* g);  // occupancy queries, before any stream capture
     int (*init)(const ip_graph* g, const Params& P, cudaStream_t st);
     // exchange + apply of one superstep in `mode`; with ev (4 events), the boundaries
@@ -74,8 +75,10 @@ __global__ void k_ctl_init(Params P) {
     c->err = 0;
     c->prev_bcast = 0;
     c->pr_delta = 0.0;
+    c->n_pull = 0;
     c->t_prev = globaltimer();
     c->n_active = P.V;
+    if (P.pb.on) P.pb.ctr[0] = P.pb.ctr[1] = 0;  // the blocked pull's task counters
     c->rq_len = 0;
     c->q_valid = 0;  // the first push-sparse exchange compacts the bitmap into queues
     for (int p = 0; p < 2; ++p)
@@ -511,6 +514,8 @@ int cuda_err(cudaError_t e);
 // Launch sizes and the host entry points of one program's kernels.
 template <class PROG>
 struct ProgramEngine {
+    static_assert(!PROG::kBlockedMinPull || std::is_same<typename PROG::Combiner, ipregel::MinCombiner<uint32_t>>::value,
+                  "the blocked pull folds uint32 broadcast slots with min");
     enum { K_PUSH_S, K_PUSH_D, K_PULL, K_PULL_EARLY, K_MISC, K_COUNT };
     static int occ[K_COUNT];  // resident CTAs per SM of each kernel, queried once
     static std::once_flag once;
@@ -560,7 +565,10 @@ struct ProgramEngine {
                 break;
             default:
                 mark(1);
-                if (PROG::kEarlyExitUnweighted && P.pull_early_exit)
+                if (PROG::kBlockedMinPull && P.pb.on) {
+                    const int r = pb_min_launch(g, P, st);
+                    if (r != IP_OK) return r;
+                } else if (PROG::kEarlyExitUnweighted && P.pull_early_exit)
                     eng::k_pull<PROG, true><<<n * occ[K_PULL_EARLY], BLOCK, 0, st>>>(P);
                 else
                     eng::k_pull<PROG, false><<<n * occ[K_PULL], BLOCK, 0, st>>>(P);
@@ -577,6 +585,7 @@ struct ProgramEngine {
         o.name = name;
         o.uses_source = PROG::kUsesSource;
         o.float_values = std::is_floating_point<typename PROG::Value>::value;
+        o.blocked_min_pull = PROG::kBlockedMinPull;
         o.prepare = &prepare;
         o.init = &init;
         o.superstep = &superstep;

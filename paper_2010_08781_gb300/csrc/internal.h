@@ -43,6 +43,7 @@ struct DevCtl {
     unsigned int pr_stale;  // PageRank: the broadcasts of the last superstep were not written (blocked pull)
     unsigned long long t_prev;  // %globaltimer at the previous selector call
     double pr_delta;        // PageRank with a tolerance: sum over vertices of |rank change| this superstep
+    unsigned int n_pull;    // pull exchanges of this run (the blocked min pull is built once they add up)
 };
 
 // One record per superstep, written by the selector kernel.
@@ -85,6 +86,10 @@ struct Bins {
 // accumulates every bin in shared memory. Device pointers of that layout.
 constexpr uint32_t PB_BIN_V = 24576;  // most destinations per bin (one 32-bit accumulator word each in shared memory)
 constexpr uint64_t PB_AUTO_EDGES = 1ull << 24;  // IP_PR_ENGINE_AUTO picks the blocked pull from this many edges
+// A min program's AUTO pull switches to the blocked layout once the handle has run this
+// many pull exchanges with the gather kernel: building the layout costs about as much
+// as that many gather exchanges (measured at R-MAT 26: about 70 ms against 6.7 ms each)
+constexpr uint64_t PB_MIN_BUILD_PULLS = 10;
 struct PbDev {
     uint32_t on;             // 1: PageRank pull runs on this layout
     uint32_t n_chunks, n_tasks;
@@ -256,6 +261,7 @@ struct ip_graph {
     uint32_t* bin_cnt = nullptr;     // [3] device counters of the degree-bin builder
     uint32_t* new_of_old = nullptr;  // renumbered graph (ip_graph_relabel): caller's id -> internal id
     uint32_t* old_of_new = nullptr;  // internal id -> caller's id
+    uint64_t pull_gathered = 0;      // pull exchanges of min programs run by the gather kernel on this handle
 };
 
 namespace ipg {
@@ -269,6 +275,8 @@ void free_batch_state(ip_graph* g);
 // pb.cu
 int pb_prepare(ip_graph* g, cudaStream_t st, PbDev* out);
 int pb_launch(const ip_graph* g, const Params& P, cudaStream_t st);
+int pb_min_launch(const ip_graph* g, const Params& P, cudaStream_t st);  // blocked pull of a min program
+int pb_set_mode(ip_graph* g, int min_mode, cudaStream_t st);  // neutral tail codes: 0 PageRank, 1 min programs
 bool pb_supported(const ip_graph* g);
 void pb_free(ip_graph* g);
 size_t pb_bytes(const ip_graph* g);  // device bytes of the blocked layout (0 if not built)

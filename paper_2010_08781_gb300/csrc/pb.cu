@@ -80,6 +80,57 @@ __device__ __forceinline__ void pb_fixed(float v, int S, uint32_t& xl, uint32_t&
 }
 
 // ---------------------------------------------------------------- phase 1
+// Copies the codes of one staged chunk (scode[i]: the code of source s0 + i,
+// scode[ns]: the code of the padding entries) into every run of the chunk at the
+// run's place in its bin. A warp takes windows of 32 consecutive runs (lengths
+// padded to 4 entries); their sources are one contiguous chunk-major range, so
+// lane k of a step reads the 4 entries a0 + 4k.. and finds their run (for the
+// bin-major place) by a search over the window. Windows are claimed one by one
+// through *next_win (shared, 0 at the start): their sizes vary.
+__device__ __forceinline__ void pb_copy_runs(const PbDev& B, const uint4& ch, const uint32_t* scode, uint32_t lane,
+                                             uint32_t* next_win) {
+    const uint32_t nwin = (ch.w - ch.z + 31) / 32;
+    for (;;) {
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(next_win, 1u);
+        wi = __shfl_sync(FULL, wi, 0);
+        if (wi >= nwin) break;
+        const uint32_t r = ch.z + 32 * wi + lane;
+        const uint4 run = r < ch.w ? __ldcs(B.runs + r) : make_uint4(0, 0, 0, 0);
+        const uint32_t a0 = __shfl_sync(FULL, run.x, 0);
+        uint32_t inc = run.z >> 2;  // inclusive prefix of the runs' groups of 4
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= (uint32_t)o) inc += y;
+        }
+        const uint32_t total = __shfl_sync(FULL, inc, 31);
+        const uint32_t delta = run.y - run.x;  // bin-major minus chunk-major place (mod 2^32)
+        for (uint32_t k0 = 0; k0 < total; k0 += 32u * PB1_LOADS) {
+            uint2 sv[PB1_LOADS];
+            uint32_t out[PB1_LOADS];
+#pragma unroll
+            for (int u = 0; u < PB1_LOADS; ++u) {
+                const uint32_t k = k0 + 32u * u + lane;
+                uint32_t j = 0;  // run of group k: the runs that end at or before it
+#pragma unroll
+                for (uint32_t st = 16; st; st >>= 1) {
+                    const uint32_t y = __shfl_sync(FULL, inc, j + st - 1);
+                    if (y <= k) j += st;
+                }
+                out[u] = __shfl_sync(FULL, delta, j) + a0 + 4 * k;
+                sv[u] = k < total ? __ldcs(reinterpret_cast<const uint2*>(B.src + a0 + 4 * k)) : make_uint2(0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < PB1_LOADS; ++u)
+                if (k0 + 32u * u + lane < total)
+                    *reinterpret_cast<uint4*>(B.code + out[u]) =
+                        make_uint4(scode[sv[u].x & 0xFFFF], scode[sv[u].x >> 16], scode[sv[u].y & 0xFFFF],
+                                   scode[sv[u].y >> 16]);
+        }
+    }
+}
+
 // Staging turns every source's broadcast into its 32-bit code once: the
 // fixed-point value itself below 2^31, else 2^31 | source with the 64-bit value
 // in big[source]. Then every warp copies whole runs, lane by lane.
@@ -131,50 +182,7 @@ __global__ void __launch_bounds__(PB1_THREADS) k_pb_scatter(Params P) {
             next_win = 0;
         }
         __syncthreads();
-        // a warp takes windows of 32 consecutive runs (lengths padded to 4 entries);
-        // their sources are one contiguous chunk-major range, so lane k of a step
-        // reads the 4 entries a0 + 4k.. and finds their run (for the bin-major
-        // place) by a search over the window
-        const uint32_t nwin = (ch.w - ch.z + 31) / 32;
-        for (;;) {  // windows are claimed one by one: their sizes vary
-            uint32_t wi = 0;
-            if (lane == 0) wi = atomicAdd(&next_win, 1u);
-            wi = __shfl_sync(FULL, wi, 0);
-            if (wi >= nwin) break;
-            const uint32_t r = ch.z + 32 * wi + lane;
-            const uint4 run = r < ch.w ? __ldcs(B.runs + r) : make_uint4(0, 0, 0, 0);
-            const uint32_t a0 = __shfl_sync(FULL, run.x, 0);
-            uint32_t inc = run.z >> 2;  // inclusive prefix of the runs' groups of 4
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(FULL, inc, o);
-                if (lane >= (uint32_t)o) inc += y;
-            }
-            const uint32_t total = __shfl_sync(FULL, inc, 31);
-            const uint32_t delta = run.y - run.x;  // bin-major minus chunk-major place (mod 2^32)
-            for (uint32_t k0 = 0; k0 < total; k0 += 32u * PB1_LOADS) {
-                uint2 sv[PB1_LOADS];
-                uint32_t out[PB1_LOADS];
-#pragma unroll
-                for (int u = 0; u < PB1_LOADS; ++u) {
-                    const uint32_t k = k0 + 32u * u + lane;
-                    uint32_t j = 0;  // run of group k: the runs that end at or before it
-#pragma unroll
-                    for (uint32_t st = 16; st; st >>= 1) {
-                        const uint32_t y = __shfl_sync(FULL, inc, j + st - 1);
-                        if (y <= k) j += st;
-                    }
-                    out[u] = __shfl_sync(FULL, delta, j) + a0 + 4 * k;
-                    sv[u] = k < total ? __ldcs(reinterpret_cast<const uint2*>(B.src + a0 + 4 * k)) : make_uint2(0, 0);
-                }
-#pragma unroll
-                for (int u = 0; u < PB1_LOADS; ++u)
-                    if (k0 + 32u * u + lane < total)
-                        *reinterpret_cast<uint4*>(B.code + out[u]) =
-                            make_uint4(scode[sv[u].x & 0xFFFF], scode[sv[u].x >> 16], scode[sv[u].y & 0xFFFF],
-                                       scode[sv[u].y >> 16]);
-            }
-        }
+        pb_copy_runs(B, ch, scode, lane, &next_win);
         __syncthreads();
     }
 }
@@ -282,6 +290,48 @@ __device__ __forceinline__ bool pb_consumer_sync(uint32_t bar, uint32_t parity, 
     return __shfl_sync(FULL, ok ? 1u : 0u, 0) != 0;
 }
 
+// Phase 2's producer (lane 0 of warp 0): claims bins in order (B.ctr[1]) and
+// streams each bin's codes and destinations in tiles of PB_TILE entries with bulk
+// copies into the PB_STAGES-stage ring (full/empty mbarriers); meta[2 st] =
+// {first vertex, vertices, tile, tiles} (first vertex INF: no more bins),
+// meta[2 st + 1].x = entries of the tile. On a timeout it records error bit 2 and
+// waits (bounded) for its copies still in flight.
+__device__ __forceinline__ void pb_produce(const Params& P, uint32_t* ring_code, uint16_t* ring_dst, uint4* meta,
+                                           uint32_t full0, uint32_t empty0) {
+    const PbDev& B = P.pb;
+    uint32_t k = 0;
+    bool ok = true;
+    for (bool more = true; more && ok;) {
+        const uint32_t t = atomicAdd(B.ctr + 1, 1u);
+        more = t < B.n_tasks;
+        const uint4 tk = more ? B.tasks[t] : make_uint4(0, 0, 0, 0);
+        const uint32_t n = tk.w - tk.z;
+        const uint32_t ntiles = more ? max(1u, (n + PB_TILE - 1) / PB_TILE) : 1u;
+        for (uint32_t j = 0; j < ntiles; ++j, ++k) {
+            const uint32_t st = k % PB_STAGES, r = k / PB_STAGES;
+            if (r >= 1 && !pb_mbar_wait(empty0 + 8 * st, (r - 1) & 1)) {
+                ok = false;
+                break;
+            }
+            const uint32_t cnt = more ? min(PB_TILE, n - j * PB_TILE) : 0u;
+            meta[2 * st] = make_uint4(more ? tk.x : INF, tk.y, j, ntiles);  // {first vertex, vertices, tile, tiles}
+            meta[2 * st + 1] = make_uint4(cnt, 0, 0, 0);
+            if (cnt) {
+                pb_mbar_arrive_tx(full0 + 8 * st, cnt * 6u);
+                pb_bulk_load(pb_smem(ring_code + st * PB_TILE), B.code + tk.z + j * PB_TILE, cnt * 4u, full0 + 8 * st);
+                pb_bulk_load(pb_smem(ring_dst + st * PB_TILE), B.dst + tk.z + j * PB_TILE, cnt * 2u, full0 + 8 * st);
+            } else {
+                pb_mbar_arrive(full0 + 8 * st);
+            }
+        }
+    }
+    if (!ok) {  // record the timeout, then wait (bounded) for the copies still in flight
+        atomicOr(&P.ctl->err, 2u);
+        for (uint32_t q = k > PB_STAGES ? k - PB_STAGES : 0; q < k; ++q)
+            (void)pb_mbar_wait(full0 + 8 * (q % PB_STAGES), (q / PB_STAGES) & 1);
+    }
+}
+
 // Phase 2. Warp 0 is the producer: one thread claims bins and streams each
 // bin's codes and destinations in tiles of PB_TILE entries with bulk copies
 // into a ring of PB_STAGES shared-memory stages (full/empty mbarriers). The
@@ -323,38 +373,7 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
     __syncthreads();
 
     if (warp == 0) {  // ------------------------------------------------ producer
-        if (lane != 0) return;
-        uint32_t k = 0;
-        bool ok = true;
-        for (bool more = true; more && ok;) {
-            const uint32_t t = atomicAdd(B.ctr + 1, 1u);
-            more = t < B.n_tasks;
-            const uint4 tk = more ? B.tasks[t] : make_uint4(0, 0, 0, 0);
-            const uint32_t n = tk.w - tk.z;
-            const uint32_t ntiles = more ? max(1u, (n + PB_TILE - 1) / PB_TILE) : 1u;
-            for (uint32_t j = 0; j < ntiles; ++j, ++k) {
-                const uint32_t st = k % PB_STAGES, r = k / PB_STAGES;
-                if (r >= 1 && !pb_mbar_wait(empty0 + 8 * st, (r - 1) & 1)) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t cnt = more ? min(PB_TILE, n - j * PB_TILE) : 0u;
-                meta[2 * st] = make_uint4(more ? tk.x : INF, tk.y, j, ntiles);  // {first vertex, vertices, tile, tiles}
-                meta[2 * st + 1] = make_uint4(cnt, 0, 0, 0);
-                if (cnt) {
-                    pb_mbar_arrive_tx(full0 + 8 * st, cnt * 6u);
-                    pb_bulk_load(pb_smem(ring_code + st * PB_TILE), B.code + tk.z + j * PB_TILE, cnt * 4u, full0 + 8 * st);
-                    pb_bulk_load(pb_smem(ring_dst + st * PB_TILE), B.dst + tk.z + j * PB_TILE, cnt * 2u, full0 + 8 * st);
-                } else {
-                    pb_mbar_arrive(full0 + 8 * st);
-                }
-            }
-        }
-        if (!ok) {  // record the timeout, then wait (bounded) for the copies still in flight
-            atomicOr(&P.ctl->err, 2u);
-            for (uint32_t q = k > PB_STAGES ? k - PB_STAGES : 0; q < k; ++q)
-                (void)pb_mbar_wait(full0 + 8 * (q % PB_STAGES), (q / PB_STAGES) & 1);
-        }
+        if (lane == 0) pb_produce(P, ring_code, ring_dst, meta, full0, empty0);
         return;
     }
 
@@ -424,6 +443,148 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
         }
     }
     flush_delta(P, dacc);  // every consumer warp leaves the loop whole (warp-uniform breaks)
+}
+
+// ---------------------------------------------------------------- min programs
+// The same layout and the same two phases for a vertex program whose combiner is
+// the uint32 minimum and whose message is the sender's value itself (Hashmin,
+// Fig. 9): the codes are the broadcast slots (the no-broadcast pattern for a vertex
+// that did not broadcast, which also fills the padding entries and the bin tails,
+// so they change nothing), and a bin folds its codes with a shared-memory atomicMin
+// per destination. A destination whose minimum is a message is a recipient (no
+// message of such a program equals the pattern): its mailbox gets the minimum and
+// its recipient bit is set, and the apply kernel runs compute() as after any pull.
+__global__ void __launch_bounds__(PB1_THREADS) k_pbm_scatter(Params P) {
+    extern __shared__ uint32_t scode[];
+    __shared__ uint32_t task, next_win;
+    const PbDev& B = P.pb;
+    const uint32_t lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) B.ctr[1] = 0;  // phase 2 of this superstep claims from 0
+    for (;;) {
+        if (threadIdx.x == 0) task = atomicAdd(B.ctr, 1u);
+        __syncthreads();
+        const uint32_t c = task;
+        if (c >= B.n_chunks) break;
+        const uint4 ch = B.chunk[c];  // {first source, sources, first run, end run}
+        const uint32_t s0 = ch.x, ns = ch.y;
+        for (uint32_t i0 = threadIdx.x; i0 < ns; i0 += PB_BATCH * blockDim.x) {  // PB_BATCH loads in flight
+            uint32_t x[PB_BATCH];
+#pragma unroll
+            for (int u = 0; u < PB_BATCH; ++u) {
+                const uint32_t i = i0 + u * blockDim.x;
+                x[u] = i < ns ? P.outbox[s0 + i] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < PB_BATCH; ++u) {
+                const uint32_t i = i0 + u * blockDim.x;
+                if (i < ns) scode[i] = x[u];
+            }
+        }
+        if (threadIdx.x == 0) {
+            scode[ns] = ipregel::kNoBroadcastBits;  // source of the padding entries
+            next_win = 0;
+        }
+        __syncthreads();
+        pb_copy_runs(B, ch, scode, lane, &next_win);
+        __syncthreads();
+    }
+}
+
+// compute() input of the bin's vertices first, first + stride, ... < nv (vertex v0 +
+// v): every lane of a warp takes consecutive vertices, so the warp's recipient bits
+// are one ballot (shifted into the one or two bitmap words it overlaps). Resets the
+// accumulators for the next bin.
+__device__ __forceinline__ void pbm_finish(const Params& P, uint32_t* acc, uint32_t v0, uint32_t nv, uint32_t first,
+                                           uint32_t stride, uint32_t lane) {
+    for (uint32_t base = first - lane; base < nv; base += stride) {
+        const uint32_t v = base + lane;
+        const bool in = v < nv;
+        const uint32_t m = in ? acc[v] : ipregel::kNoBroadcastBits;
+        if (in) acc[v] = ipregel::kNoBroadcastBits;
+        const bool r = m != ipregel::kNoBroadcastBits;
+        if (r) P.mbox[v0 + v] = m;
+        const uint32_t bits = __ballot_sync(FULL, r);
+        if (lane == 0 && bits) {
+            const uint32_t gv = v0 + base, w = gv >> 5, sh = gv & 31u;
+            atomicOr(P.recv + w, bits << sh);
+            if (sh && (bits >> (32 - sh))) atomicOr(P.recv + w + 1, bits >> (32 - sh));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pbm_accumulate(Params P) {
+    extern __shared__ __align__(128) uint32_t acc[];                              // [PB_BIN_V]
+    uint32_t* ring_code = acc + PB_BIN_V;                                          // [PB_STAGES][PB_TILE]
+    uint16_t* ring_dst = reinterpret_cast<uint16_t*>(ring_code + PB_STAGES * PB_TILE);  // [PB_STAGES][PB_TILE]
+    uint4* meta = reinterpret_cast<uint4*>(ring_dst + PB_STAGES * PB_TILE);     // [PB_STAGES][2]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(meta + 2 * PB_STAGES);         // full[PB_STAGES], empty[PB_STAGES]
+    __shared__ __align__(8) uint64_t cbar[2];                                  // consumer barriers
+    const PbDev& B = P.pb;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t full0 = pb_smem(bars), empty0 = pb_smem(bars + PB_STAGES);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < PB_STAGES; ++i) {
+            pb_mbar_init(full0 + 8 * i, 1);
+            pb_mbar_init(empty0 + 8 * i, PB2_CONSUMERS);
+        }
+        pb_mbar_init(pb_smem(cbar), PB2_CONSUMERS);
+        pb_mbar_init(pb_smem(cbar + 1), PB2_CONSUMERS);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        if (blockIdx.x == 0) B.ctr[0] = 0;  // phase 1 of the next superstep claims from 0
+    }
+    for (uint32_t i = threadIdx.x; i < PB_BIN_V; i += blockDim.x) acc[i] = ipregel::kNoBroadcastBits;
+    __syncthreads();
+    if (warp == 0) {  // producer
+        if (lane == 0) pb_produce(P, ring_code, ring_dst, meta, full0, empty0);
+        return;
+    }
+    const uint32_t c = threadIdx.x - 32;  // 0 .. 32 * PB2_CONSUMERS - 1
+    const uint32_t cb0 = pb_smem(cbar), cb1 = pb_smem(cbar + 1);
+    uint32_t bins_done = 0;
+    for (uint32_t k = 0;; ++k) {
+        const uint32_t st = k % PB_STAGES, r = k / PB_STAGES;
+        if (!pb_mbar_wait(full0 + 8 * st, r & 1)) {
+            atomicOr(&P.ctl->err, 2u);
+            break;
+        }
+        const uint4 m = meta[2 * st];  // {first vertex, vertices, tile, tiles}
+        const uint32_t cnt = meta[2 * st + 1].x;
+        if (m.x == INF) break;
+#pragma unroll
+        for (int gq = 0; gq < PB_GROUPS; ++gq) {
+            const uint32_t i = 4 * (c + gq * 32 * PB2_CONSUMERS);
+            if (i < cnt) {
+                const uint4 cv = *reinterpret_cast<const uint4*>(ring_code + st * PB_TILE + i);
+                const uint2 dv = *reinterpret_cast<const uint2*>(ring_dst + st * PB_TILE + i);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t code = q == 0 ? cv.x : q == 1 ? cv.y : q == 2 ? cv.z : cv.w;
+                    const uint32_t d = ((q < 2 ? dv.x : dv.y) >> (16 * (q & 1))) & 0xFFFFu;
+                    if (code != ipregel::kNoBroadcastBits) atomicMin(acc + d, code);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) pb_mbar_arrive(empty0 + 8 * st);
+        if (m.z + 1 == m.w) {  // the bin's last tile: every code is in
+            bool ok = pb_consumer_sync(cb0, bins_done & 1, lane);
+            pbm_finish(P, acc, m.x, m.y, c, 32 * PB2_CONSUMERS, lane);
+            ok = pb_consumer_sync(cb1, bins_done & 1, lane) && ok;
+            ++bins_done;
+            if (!ok) {
+                if (lane == 0) atomicOr(&P.ctl->err, 2u);
+                break;
+            }
+        }
+    }
+}
+
+// Sets the codes of the bin tails (the entries between a bin's last run and the
+// next bin, which no scatter writes) to the neutral code of an engine: 0 for the
+// PageRank sums, the no-broadcast pattern for the min programs.
+__global__ void k_pb_tails(uint32_t* code, const uint2* tails, uint32_t nb, uint32_t value) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += gridDim.x * blockDim.x)
+        for (uint32_t e = tails[q].x; e < tails[q].y; ++e) code[e] = value;
 }
 
 // ---------------------------------------------------------------- layout build
@@ -567,7 +728,9 @@ __global__ void __launch_bounds__(PBB_THREADS) k_pb_place(const uint32_t* __rest
 struct PbLayout {
     PbDev d;
     std::vector<std::pair<void*, size_t>> bufs;
-    int grid1 = 0, grid2 = 0;
+    int grid1 = 0, grid2 = 0, grid1m = 0;
+    uint2* tails = nullptr;  // [n_tasks] bin tails {first entry, end entry}
+    int tail_mode = 0;       // 0: tail codes 0 (PageRank), 1: no-broadcast pattern (min programs)
 };
 
 template <class T>
@@ -632,7 +795,10 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     PbDev& d = L->d;
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB1_SMEM)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB2_SMEM)));
+    PBK(cuda_err(cudaFuncSetAttribute(k_pbm_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB1_SMEM)));
+    PBK(cuda_err(cudaFuncSetAttribute(k_pbm_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB2_SMEM)));
     L->grid1 = occupancy_grid(g, (const void*)k_pb_scatter, PB1_THREADS, PB1_SMEM);
+    L->grid1m = occupancy_grid(g, (const void*)k_pbm_scatter, PB1_THREADS, PB1_SMEM);
     L->grid2 = g->num_sms;  // one producer/consumer CTA per SM
 
     // chunks of consecutive sources, cut by edge count and by source count; runs of
@@ -745,14 +911,20 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
                                                         d_bbase, nb, d_M, d_runs, d_src, d_dst);
     PBK(cuda_err(cudaGetLastError()));
 
-    // phase-2 tasks, one per bin, in bin order
+    // phase-2 tasks, one per bin, in bin order; the tail of every bin (entries after its runs)
     std::vector<uint4> tasks(nb);
-    for (uint32_t q = 0; q < nb; ++q) tasks[q] = make_uint4(bstart[q], bstart[q + 1] - bstart[q], bbase[q], bbase[q + 1]);
+    std::vector<uint2> tails(nb);
+    for (uint32_t q = 0; q < nb; ++q) {
+        tasks[q] = make_uint4(bstart[q], bstart[q + 1] - bstart[q], bbase[q], bbase[q + 1]);
+        tails[q] = make_uint2(bbase[q] + total[q], bbase[q + 1]);
+    }
     uint4* d_tasks;
     uint32_t* d_ctr;
     PBK(pb_alloc(g, L, &d_tasks, nb));
     PBK(pb_alloc(g, L, &d_ctr, 2));
+    PBK(pb_alloc(g, L, &L->tails, nb));
     PBK(cuda_err(cudaMemcpyAsync(d_tasks, tasks.data(), sizeof(uint4) * nb, cudaMemcpyHostToDevice, st)));
+    PBK(cuda_err(cudaMemcpyAsync(L->tails, tails.data(), sizeof(uint2) * nb, cudaMemcpyHostToDevice, st)));
     PBK(cuda_err(cudaMemsetAsync(d_ctr, 0, sizeof(uint32_t) * 2, st)));
     PBK(cuda_err(cudaStreamSynchronize(st)));
 
@@ -798,6 +970,24 @@ int pb_launch(const ip_graph* g, const Params& P, cudaStream_t st) {
     k_pb_scatter<<<L->grid1, PB1_THREADS, PB1_SMEM, st>>>(P);
     k_pb_accumulate<<<L->grid2, 32 * (PB2_CONSUMERS + 1), PB2_SMEM, st>>>(P);
     return cuda_err(cudaGetLastError());
+}
+
+int pb_min_launch(const ip_graph* g, const Params& P, cudaStream_t st) {
+    const PbLayout* L = static_cast<const PbLayout*>(g->pb);
+    k_pbm_scatter<<<L->grid1m, PB1_THREADS, PB1_SMEM, st>>>(P);
+    k_pbm_accumulate<<<L->grid2, 32 * (PB2_CONSUMERS + 1), PB2_SMEM, st>>>(P);
+    return cuda_err(cudaGetLastError());
+}
+
+int pb_set_mode(ip_graph* g, int min_mode, cudaStream_t st) {
+    PbLayout* L = static_cast<PbLayout*>(g->pb);
+    if (!L || L->tail_mode == min_mode) return IP_OK;
+    const uint32_t nb = L->d.n_tasks;
+    k_pb_tails<<<std::max<uint32_t>(1, (nb + 255) / 256), 256, 0, st>>>(L->d.code, L->tails, nb,
+                                                                         min_mode ? ipregel::kNoBroadcastBits : 0u);
+    const int r = cuda_err(cudaGetLastError());
+    if (r == IP_OK) L->tail_mode = min_mode;
+    return r;
 }
 
 size_t pb_bytes(const ip_graph* g) {

@@ -335,6 +335,7 @@ __global__ void k_select(Params P) {
             mode = f[6] < P.thr_sparse ? IP_MODE_PUSH_SPARSE : (f[6] >= P.thr_pull ? IP_MODE_PULL : IP_MODE_PUSH_DENSE);
     }
     if (P.app == APP_PR && mode == IP_MODE_PUSH_SPARSE) mode = IP_MODE_PUSH_DENSE;  // every vertex broadcasts
+    if (!done && mode == IP_MODE_PULL && threadIdx.x == 0) ++c->n_pull;
     __syncwarp();
     if (threadIdx.x == 0) {
         if (s < P.log_cap) {
@@ -776,6 +777,18 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
             const int r = pb_prepare(g, st, &P.pb);
             // AUTO keeps the gather engine where the layout does not fit (entries beyond 2^32)
             if (r != IP_OK && !(r == IP_E_RANGE && o.pr_engine == IP_PR_ENGINE_AUTO)) return r;
+            if (P.pb.on) CKR(pb_set_mode(g, 0, st));
+        }
+    } else if (ops->blocked_min_pull) {
+        // the blocked pull of a min program: forced, or (AUTO) once the layout exists or this
+        // handle's gather pulls have cost about as much as building it (PB_MIN_BUILD_PULLS)
+        const bool blocked = o.pr_engine == IP_PR_ENGINE_BLOCKED ||
+                             (o.pr_engine == IP_PR_ENGINE_AUTO && g->E >= PB_AUTO_EDGES && pb_supported(g) &&
+                              (g->pb || g->pull_gathered >= PB_MIN_BUILD_PULLS));
+        if (blocked) {
+            const int r = pb_prepare(g, st, &P.pb);
+            if (r != IP_OK && !(r == IP_E_RANGE && o.pr_engine == IP_PR_ENGINE_AUTO)) return r;
+            if (P.pb.on) CKR(pb_set_mode(g, 1, st));
         }
     }
 
@@ -803,6 +816,7 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     const DevCtl& c = *g->ctl_host;
     const uint32_t supersteps = c.superstep + 1;
     g->last_app = app;
+    if (ops && ops->blocked_min_pull && !P.pb.on) g->pull_gathered += c.n_pull;
     if (c.err & 2u) return IP_E_TIMEOUT;  // a bounded wait of a kernel ran out
     if (c.err) return IP_E_DEVICE_ASSERT;
     if (stats) {
