@@ -470,21 +470,43 @@ def run_gpu(args, rank, world, local_rank):
     out_f = torch.empty(V, dtype=torch.float32).pin_memory()
     out_u = torch.empty(V, dtype=torch.int32).pin_memory()
     e2e_ms = []
+    phases = {k: [] for k in ("create_directed", "pagerank_run", "pagerank_device", "values_pagerank",
+                              "destroy_directed", "create_symmetrised", "hashmin_run", "hashmin_device",
+                              "values_hashmin", "destroy_symmetrised")}
+
+    def lap(name, t):
+        torch.cuda.synchronize()
+        now = time.perf_counter()
+        phases[name].append(1e3 * (now - t))
+        return now
+
     for i in range(e2e_steps):
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        with ipg.Graph(V, pin["d_ptr"], pin["d_col"], stream=stream) as A:
-            A.run("pagerank", **pr_kw)
-            A.values(out=out_f, stream=stream)
-        with ipg.Graph(V, pin["s_ptr"], pin["s_col"], symmetric=True, stream=stream) as B:
-            B.run("hashmin", **hm_kw)
-            B.values(out=out_u, stream=stream)
-        torch.cuda.synchronize()
-        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        t0 = t = time.perf_counter()
+        A = ipg.Graph(V, pin["d_ptr"], pin["d_col"], stream=stream)
+        t = lap("create_directed", t)
+        ra = A.run("pagerank", **pr_kw)
+        t = lap("pagerank_run", t)
+        A.values(out=out_f, stream=stream)
+        t = lap("values_pagerank", t)
+        A.close()
+        t = lap("destroy_directed", t)
+        B = ipg.Graph(V, pin["s_ptr"], pin["s_col"], symmetric=True, stream=stream)
+        t = lap("create_symmetrised", t)
+        rb = B.run("hashmin", **hm_kw)
+        t = lap("hashmin_run", t)
+        B.values(out=out_u, stream=stream)
+        t = lap("values_hashmin", t)
+        B.close()
+        t = lap("destroy_symmetrised", t)
+        phases["pagerank_device"].append(ra.elapsed_ms)
+        phases["hashmin_device"].append(rb.elapsed_ms)
+        e2e_ms.append(1e3 * (t - t0))
     h2d = 4 * (V + 1) + 4 * Ed + 4 * (V + 1) + 4 * Es
     e2e = {"value": round((msgs / args.steps) / (statistics.median(e2e_ms) * 1e-3) / 1e9, 3), "unit": "GTEPS",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 2 * 4 * V, "steps": e2e_steps,
            "median_step_ms": round(statistics.median(e2e_ms), 2),
+           "phases_median_ms": {k: round(statistics.median(v), 2) for k, v in phases.items()},
            "covers": "graph creation from pinned host CSR (device transposition, renumbering, degree bins, "
                      "blocked layout), both runs, results copied to pinned host memory, destroy"}
     del pin

@@ -83,8 +83,8 @@ typedef enum {
  * they differ in how the in-neighbours' broadcasts reach the destination. */
 typedef enum {
     IP_PR_ENGINE_AUTO = 0,    /* PageRank: BLOCKED on graphs of at least 2^24 edges that it supports,
-                                 else GATHER. Hashmin: GATHER until the handle has run 10 gather pulls
-                                 (the layout costs about as much to build), BLOCKED from then on (or
+                                 else GATHER. Hashmin: GATHER until the handle has run 6 gather pulls
+                                 (a handle that is run again and again), BLOCKED from then on (or
                                  whenever the layout already exists) on graphs of at least 2^24 edges */
     IP_PR_ENGINE_GATHER = 1,  /* every in-edge of the CSC reads its source's broadcast */
     IP_PR_ENGINE_BLOCKED = 2  /* two streaming passes over a second edge layout built on first use
@@ -367,9 +367,9 @@ int ip_hashmin_noalloc(uint32_t n_vertices, uint64_t n_edges, const uint32_t* cs
 
 /* Device memory. A graph's device buffers come from a process-wide cache kept by
  * the library: ip_graph_destroy synchronises the graph's device and returns the
- * buffers to the cache (at most 32 GiB stay cached), and an allocation of the same
- * size on the same device reuses one, so building graphs of the same shape again
- * and again allocates once. An allocation that fails releases the cache of its
+ * buffers to the cache (at most a quarter of the device's memory, up to 64 GiB,
+ * stay cached), and an allocation of the same size on the same device reuses one,
+ * so building graphs of the same shape again and again allocates once. An allocation that fails releases the cache of its
  * device and retries. The paper has no counterpart (its graphs are built once).
  * ip_release_cached_memory frees every cached buffer on every device and returns
  * IP_OK; the cache is guarded by a lock, so any thread may call it. */

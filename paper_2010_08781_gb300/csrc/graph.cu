@@ -39,10 +39,21 @@ int cuda_err(cudaError_t e) {
 // synchronisation) instead of freeing them, and the next allocation of the same
 // size on the same device takes one back: a caller that builds graphs of the same
 // shape again and again pays cudaMalloc / cudaFree (which synchronises) once. At
-// most DEV_CACHE_CAP bytes stay cached; an allocation that fails first releases
-// the cache of its device; ip_release_cached_memory() releases everything.
+// most dev_cache_cap() bytes stay cached (a quarter of the device's memory, at most
+// 64 GiB: two billion-edge graphs); an allocation that fails first releases the
+// cache of its device; ip_release_cached_memory() releases everything.
 namespace {
-constexpr size_t DEV_CACHE_CAP = 32ull << 30;
+size_t dev_cache_cap() {
+    static const size_t cap = [] {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return (size_t)32 << 30;
+        }
+        return std::min<size_t>((size_t)64 << 30, total_b / 4);
+    }();
+    return cap;
+}
 struct DeviceCache {
     std::mutex m;
     std::unordered_map<void*, std::pair<int, size_t>> live;   // buffers handed out: device, size
@@ -83,7 +94,7 @@ void dcache_release(void* p) {
     }
     const std::pair<int, size_t> key = it->second;
     C.live.erase(it);
-    if (C.cached_bytes + key.second <= DEV_CACHE_CAP) {
+    if (C.cached_bytes + key.second <= dev_cache_cap()) {
         C.cached.insert({key, p});
         C.cached_bytes += key.second;
     } else {

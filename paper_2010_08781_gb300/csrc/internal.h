@@ -87,9 +87,11 @@ struct Bins {
 constexpr uint32_t PB_BIN_V = 24576;  // most destinations per bin (one 32-bit accumulator word each in shared memory)
 constexpr uint64_t PB_AUTO_EDGES = 1ull << 24;  // IP_PR_ENGINE_AUTO picks the blocked pull from this many edges
 // A min program's AUTO pull switches to the blocked layout once the handle has run this
-// many pull exchanges with the gather kernel: building the layout costs about as much
-// as that many gather exchanges (measured at R-MAT 26: about 70 ms against 6.7 ms each)
-constexpr uint64_t PB_MIN_BUILD_PULLS = 10;
+// many pull exchanges with the gather kernel (two Hashmin runs on R-MAT graphs): a handle
+// that is run again and again then pays the build once (at R-MAT 26 it costs about as
+// much as ten gather exchanges, and every later exchange is 1.6x faster), while a
+// handle run once or twice never builds it
+constexpr uint64_t PB_MIN_BUILD_PULLS = 6;
 struct PbDev {
     uint32_t on;             // 1: PageRank pull runs on this layout
     uint32_t n_chunks, n_tasks;

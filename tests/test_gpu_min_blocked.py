@@ -76,7 +76,7 @@ def test_layout_shared_with_pagerank():
 
 def test_auto_builds_the_layout_after_enough_gather_pulls():
     """AUTO on a graph of at least 2^24 edges: the first runs pull with the gather
-    kernel; once the handle has run 10 gather pulls the next run builds the layout
+    kernel; once the handle has run 6 gather pulls the next run builds the layout
     and uses it; the labels never change."""
     g = inputs.rmat_graph(20, symmetrize=True, seed=2)
     assert g.m >= 1 << 24
@@ -87,6 +87,6 @@ def test_auto_builds_the_layout_after_enough_gather_pulls():
             st = _check(G, ref, policy="forced", forced_mode="pull")
             if G.info()["bytes_blocked_layout"] and built_at is None:
                 built_at = run
-                assert pulls >= 10
+                assert pulls >= 6
             pulls += st.supersteps - 1
-        assert built_at is not None and built_at <= 10 // (st.supersteps - 1) + 1
+        assert built_at is not None and built_at <= 6 // (st.supersteps - 1) + 1
