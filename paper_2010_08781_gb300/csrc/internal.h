@@ -271,6 +271,7 @@ namespace ipg {
 int alloc_dev(ip_graph* g, void** p, size_t bytes);
 void free_dev(void* p);
 int ensure_bins(ip_graph* g, uint32_t t1, uint32_t t2, cudaStream_t st);
+int exclusive_scan(ip_graph* g, uint32_t* data, uint64_t n, cudaStream_t st);  // in place, n uint32
 int cuda_err(cudaError_t e);
 // batch.cu
 void free_batch_state(ip_graph* g);

@@ -724,6 +724,44 @@ __global__ void __launch_bounds__(PBB_THREADS) k_pb_place(const uint32_t* __rest
     }
 }
 
+// Cuts of a vertex range into consecutive groups (chunks of sources over the CSR
+// offsets, bins of destinations over the CSC offsets), greedily: a group grows while
+// it has fewer than max_n vertices and at most per_e edges (a vertex with more edges
+// than that is a group of its own). The greedy pass is sequential, but where a group
+// that starts at u ends depends on u alone: k_pb_next finds that end for every u in
+// parallel (a binary search, the offsets being sorted), and k_pb_walk follows the
+// chain of ends from vertex 0, one dependent step per group.
+__global__ void k_pb_next(const uint32_t* __restrict__ off, uint32_t n, uint32_t per_e, uint32_t max_n,
+                          uint32_t* nxt) {
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const uint64_t lim = (uint64_t)off[u] + per_e;
+        const uint64_t end = (uint64_t)u + max_n;
+        const uint32_t cap = end < n ? (uint32_t)end : n;
+        // the group [u, j) ends at the smallest j in [u + 1, cap] with j == cap or off[j + 1] > lim
+        uint32_t lo = u + 1, hi = cap;  // answer in [lo, hi]
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo) / 2;
+            if ((uint64_t)off[mid + 1] > lim)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        nxt[u] = lo;
+    }
+}
+
+// One thread: the group starts {first vertex, its first edge} in order, at most cap of
+// them (*count = cap + 1 if the chain did not end within cap groups).
+__global__ void k_pb_walk(const uint32_t* __restrict__ nxt, const uint32_t* __restrict__ off, uint32_t n,
+                          uint32_t cap, uint2* starts, uint32_t* count) {
+    uint32_t u = 0, k = 0;
+    while (u < n && k < cap) {
+        starts[k++] = make_uint2(u, off[u]);
+        u = nxt[u];
+    }
+    *count = u < n ? cap + 1 : k;
+}
+
 // Host-side owner of the layout's device buffers.
 struct PbLayout {
     PbDev d;
@@ -770,6 +808,41 @@ struct TmpBuf {
     }
 };
 
+// The greedy group starts for the offsets off (device, n + 1 entries), read back as
+// {first vertex, its first edge} pairs in vertex order. A group that ends by the
+// vertex cap has max_n vertices; two groups in a row that end by the edge cap hold
+// more than per_e edges together: so there are at most n / max_n + 2 E / per_e + 2.
+int pb_cuts(ip_graph* g, const uint32_t* off, uint32_t n, uint64_t per_e, uint32_t max_n, cudaStream_t st,
+            std::vector<uint2>* out) {
+    const uint32_t pe = (uint32_t)std::min<uint64_t>(per_e, 0xFFFFFFFFull);
+    const uint64_t bound = (uint64_t)n / max_n + 2 * g->E / pe + 16;
+    const uint32_t cap = (uint32_t)std::min<uint64_t>(bound, n);
+    uint32_t *nxt = nullptr, *count = nullptr;
+    uint2* starts = nullptr;
+    int r = alloc_dev(g, (void**)&nxt, (size_t)n * sizeof(uint32_t));
+    if (!r) r = alloc_dev(g, (void**)&count, sizeof(uint32_t));
+    if (!r) r = alloc_dev(g, (void**)&starts, std::max<size_t>(cap, 1) * sizeof(uint2));
+    if (!r) {
+        const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)g->num_sms * 8, ((uint64_t)n + 255) / 256));
+        k_pb_next<<<grid, 256, 0, st>>>(off, n, pe, max_n, nxt);
+        k_pb_walk<<<1, 1, 0, st>>>(nxt, off, n, cap, starts, count);
+        r = cuda_err(cudaGetLastError());
+    }
+    uint32_t total = 0;
+    if (!r) r = cuda_err(cudaMemcpyAsync(&total, count, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    if (!r) r = cuda_err(cudaStreamSynchronize(st));
+    if (!r && total > cap) r = IP_E_RANGE;  // cannot happen (see the bound above)
+    if (!r) {
+        out->resize(total);
+        r = cuda_err(cudaMemcpyAsync(out->data(), starts, sizeof(uint2) * total, cudaMemcpyDeviceToHost, st));
+    }
+    if (!r) r = cuda_err(cudaStreamSynchronize(st));
+    for (void* p : {(void*)nxt, (void*)count, (void*)starts}) free_dev(p);
+    g->device_bytes -= (nxt ? (size_t)n * sizeof(uint32_t) : 0) + (count ? sizeof(uint32_t) : 0) +
+                       (starts ? std::max<size_t>(cap, 1) * sizeof(uint2) : 0);
+    return r;
+}
+
 int occupancy_grid(const ip_graph* g, const void* fn, int threads, size_t smem) {
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) {
@@ -801,35 +874,27 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     L->grid1m = occupancy_grid(g, (const void*)k_pbm_scatter, PB1_THREADS, PB1_SMEM);
     L->grid2 = g->num_sms;  // one producer/consumer CTA per SM
 
-    // chunks of consecutive sources, cut by edge count and by source count; runs of
-    // sources without out-edges that would form a chunk of their own are skipped
-    std::vector<uint32_t> off(V + 1);
-    PBK(cuda_err(cudaMemcpyAsync(off.data(), g->csr_off, sizeof(uint32_t) * (V + 1), cudaMemcpyDeviceToHost, st)));
-    PBK(cuda_err(cudaStreamSynchronize(st)));
-    std::vector<uint2> chunks;
+    // chunks of consecutive sources, cut greedily on the device (pb_cuts) by edge count
+    // and by source count; chunks of sources without out-edges are skipped
+    std::vector<uint2> cut;
     const uint64_t chunk_e = std::min<uint64_t>(PB_CHUNK_MAX, std::max<uint64_t>(PB_CHUNK_MIN, g->E >> 12));
-    for (uint32_t u = 0; u < V;) {
-        const uint32_t first = u, e0 = off[u];
-        ++u;
-        while (u < V && u - first < PB_MAXS && off[u + 1] - e0 <= chunk_e) ++u;
-        if (off[u] != e0) chunks.push_back(make_uint2(first, u - first));
+    PBK(pb_cuts(g, g->csr_off, V, chunk_e, PB_MAXS, st, &cut));
+    std::vector<uint2> chunks;
+    for (size_t i = 0; i < cut.size(); ++i) {
+        const uint32_t first = cut[i].x, next = i + 1 < cut.size() ? cut[i + 1].x : V;
+        const uint64_t e1 = i + 1 < cut.size() ? cut[i + 1].y : g->E;
+        if (e1 != cut[i].y) chunks.push_back(make_uint2(first, next - first));
     }
     const uint32_t nC = (uint32_t)chunks.size();
     // bins of consecutive destinations, cut by vertex count and by in-edge count
-    PBK(cuda_err(cudaMemcpyAsync(off.data(), g->csc_off, sizeof(uint32_t) * (V + 1), cudaMemcpyDeviceToHost, st)));
-    PBK(cuda_err(cudaStreamSynchronize(st)));
     const uint64_t bin_e = std::max<uint64_t>(16384, (g->E + 4ull * L->grid2 - 1) / (4ull * L->grid2));
-    std::vector<uint32_t> bstart{0};
-    for (uint32_t v = 0; v < V;) {
-        const uint32_t first = v, e0 = off[v];
-        ++v;
-        while (v < V && v - first < PB_BIN_V && off[v + 1] - e0 <= bin_e) ++v;
-        bstart.push_back(v);
-    }
+    PBK(pb_cuts(g, g->csc_off, V, bin_e, PB_BIN_V, st, &cut));
+    std::vector<uint32_t> bstart;
+    bstart.reserve(cut.size() + 1);
+    for (const uint2& c : cut) bstart.push_back(c.x);
+    bstart.push_back(V);
     const uint32_t nb = (uint32_t)bstart.size() - 1;
     if (nb > PB_MAX_BINS) PBK(IP_E_RANGE);
-    off.clear();
-    off.shrink_to_fit();
 
     uint4* d_cs;
     uint32_t* d_bstart;
