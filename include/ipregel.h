@@ -171,7 +171,9 @@ typedef struct {
      * Section 7.2 and Table 3; the combined one-slot mailbox of Section 4.3.3 is
      * one 4-byte word per vertex): */
     uint64_t bytes_graph;         /* CSR and CSC offsets, indices and weights (the CSC shares
-                                     the CSR's arrays for a symmetric graph) */
+                                     the CSR's arrays for a symmetric graph; a CSC built on
+                                     the device holds its offsets only until a run reads
+                                     its rows) */
     uint64_t bytes_vertex_state;  /* per-vertex values, ranks, broadcast slots, mailboxes,
                                      out-degree reciprocals, bitmaps and frontier queues */
     uint64_t bytes_degree_bins;   /* degree-binned schedules of both edge directions (every
@@ -198,7 +200,11 @@ void ip_options_default(ip_options_t* opt);
  *                edge weighs 1 for SSSP).
  *   csc_offsets / csc_rows / csc_weights  the in-edge (transposed) arrays in the
  *                same form; NULL csc_offsets means "build the transpose on the
- *                device"; csc_offsets == csr_offsets and csc_rows == csr_cols
+ *                device": its offsets at creation, its rows and weights at the
+ *                first run that reads them (a pull of a vertex program, the gather
+ *                PageRank engine, a batched run; a run that cannot allocate them
+ *                returns IP_E_NOMEM and leaves the graph as it was; PageRank with
+ *                the blocked engine never needs them); csc_offsets == csr_offsets and csc_rows == csr_cols
  *                declares a symmetric graph and shares the arrays. csc_weights
  *                is required when csc arrays and csr_weights are both given.
  *   flags        IP_CREATE_DEVICE_PTRS: all arrays are device memory (else all are

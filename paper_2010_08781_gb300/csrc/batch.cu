@@ -752,6 +752,7 @@ int ip_run_batch_sssp(ip_graph_t* g, const uint32_t* sources, uint32_t k, uint32
     BatchState* b = state_of(g);
     const uint32_t G = (k + 31) / 32;
     int r;
+    if ((r = ensure_in_rows(g, st))) return r;  // the exchange reads the in-edge rows
     if (b->ms_G != G) {  // per-vertex storage for G groups of 32 sources
         for (void* p : {(void*)b->dist, (void*)b->mbox, (void*)b->masks}) {
             if (p) free_dev(p);
@@ -862,6 +863,7 @@ int ip_run_batch_hashmin(ip_graph_t* g, const uint32_t* instance_offsets, uint32
     BatchState* b = state_of(g);
     int r;
     if ((r = ensure_bins(g, g->cur ? g->cur->t1 : DEFAULT_T1, g->cur ? g->cur->t2 : DEFAULT_T2, st))) return r;
+    if ((r = ensure_in_rows(g, st))) return r;  // both engines pull over the in-edge rows
     if ((r = ensure_small(g, b, 2 * (size_t)k + 1))) return r;
     if (!stats || stats->engine == 0) {
         // the union runs through ip_run's device-driven superstep graph, recording last sends

@@ -579,48 +579,73 @@ static int upload(ip_graph* g, uint32_t** dst, const uint32_t* src, size_t count
 
 // The CSC of g's CSR, transposed on the device (count, scan, scatter); the order
 // of a vertex's in-edges is unspecified.
-static int transpose_csr(ip_graph* g, cudaStream_t st) {
+// The transpose in two parts. Its offsets (in-degrees counted and scanned) are built
+// with the graph: the degree bins, the blocked layout's bin cuts and the maximum
+// in-degree read them. Its rows (and weights) are built by the first run that reads
+// them (ensure_in_rows): a pull of a vertex program, the gather PageRank engine or a
+// batched run. The blocked PageRank pull streams its own layout, so a graph that only
+// runs it never holds the in-edge rows.
+static int build_in_offsets(ip_graph* g, cudaStream_t st) {
     const uint32_t n = g->V;
     const uint64_t E = g->E;
-    const size_t ea = edge_alloc_count(E);
     int r;
     if ((r = alloc_dev(g, (void**)&g->csc_off, ((size_t)n + 1) * sizeof(uint32_t)))) return r;
-    if ((r = alloc_dev(g, (void**)&g->csc_row, ea * sizeof(uint32_t)))) return r;
-    CK(cudaMemsetAsync(g->csc_row + E, 0, (ea - E) * sizeof(uint32_t), st));  // the padding after the last edge
-    if (g->csr_w) {
-        if ((r = alloc_dev(g, (void**)&g->csc_w, ea * sizeof(uint32_t)))) return r;
-        CK(cudaMemsetAsync(g->csc_w + E, 0, (ea - E) * sizeof(uint32_t), st));
-    }
     CK(cudaMemsetAsync(g->csc_off, 0, ((size_t)n + 1) * sizeof(uint32_t), st));
     if (E) {
         k_count_in<<<grid_for(g, E), 256, 0, st>>>(g->csr_col, E, g->csc_off);
         CK(cudaGetLastError());
     }
     if ((r = exclusive_scan(g, g->csc_off, (uint64_t)n + 1, st))) return r;
-    uint32_t* cursor = nullptr;
-    uint32_t* chunk_src = nullptr;
+    g->csc_rows_pending = true;
+    return IP_OK;
+}
+
+// Places every out-edge (u, v) at the next free slot of v's in-edge row. On an
+// allocation failure nothing is kept: the rows stay pending.
+static int build_in_rows(ip_graph* g, cudaStream_t st) {
+    const uint32_t n = g->V;
+    const uint64_t E = g->E;
+    const size_t ea = edge_alloc_count(E);
     const uint32_t n_chunks = (uint32_t)((E + RL_CH - 1) / RL_CH);
-    if ((r = alloc_dev(g, (void**)&cursor, (size_t)n * sizeof(uint32_t)))) return r;
-    g->device_bytes -= (size_t)n * sizeof(uint32_t);
-    if ((r = alloc_dev(g, (void**)&chunk_src, std::max<size_t>(n_chunks, 1) * sizeof(uint32_t)))) {
+    const size_t tmp_bytes = (size_t)n * sizeof(uint32_t) + std::max<size_t>(n_chunks, 1) * sizeof(uint32_t);
+    uint32_t *row = nullptr, *w = nullptr, *cursor = nullptr, *chunk_src = nullptr;
+    int r = alloc_dev(g, (void**)&row, ea * sizeof(uint32_t));
+    if (!r && g->csr_w) r = alloc_dev(g, (void**)&w, ea * sizeof(uint32_t));
+    if (!r) r = alloc_dev(g, (void**)&cursor, (size_t)n * sizeof(uint32_t));
+    if (!r) r = alloc_dev(g, (void**)&chunk_src, std::max<size_t>(n_chunks, 1) * sizeof(uint32_t));
+    if (r) {
+        size_t held = 0;
+        if (row) held += ea * sizeof(uint32_t);
+        if (w) held += ea * sizeof(uint32_t);
+        if (cursor) held += (size_t)n * sizeof(uint32_t);
+        free_dev(row);
+        free_dev(w);
         free_dev(cursor);
+        g->device_bytes -= held;
         return r;
     }
-    g->device_bytes -= std::max<size_t>(n_chunks, 1) * sizeof(uint32_t);
+    g->device_bytes -= tmp_bytes;  // the cursor and chunk sources are freed below
+    g->csc_row = row;              // the handle's destroy frees them from here on
+    g->csc_w = w;
+    CK(cudaMemsetAsync(row + E, 0, (ea - E) * sizeof(uint32_t), st));  // the padding after the last edge
+    if (w) CK(cudaMemsetAsync(w + E, 0, (ea - E) * sizeof(uint32_t), st));
     CK(cudaMemcpyAsync(cursor, g->csc_off, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
     if (E) {
         k_rl_chunk_src<<<grid_for(g, n_chunks), 256, 0, st>>>(g->csr_off, n, n_chunks, chunk_src);
         k_scatter_in<<<grid_for(g, (uint64_t)n_chunks * 32), 256, 0, st>>>(g->csr_off, chunk_src, g->csr_col, g->csr_w,
-                                                                           n, E, n_chunks, cursor, g->csc_row, g->csc_w);
+                                                                           n, E, n_chunks, cursor, row, w);
     }
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(st);
     free_dev(cursor);
     free_dev(chunk_src);
+    g->csc_rows_pending = false;
     CK(e1);
     CK(e2);
     return IP_OK;
 }
+
+int ensure_in_rows(ip_graph* g, cudaStream_t st) { return g->csc_rows_pending ? build_in_rows(g, st) : IP_OK; }
 
 static int relabel(ip_graph* g, cudaStream_t st);
 
@@ -663,10 +688,10 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
         if ((r = upload(g, &g->csc_row, csc_row, E, ea, device_ptrs, st, n, &ids_checked))) return r;
         if (csc_w && (r = upload(g, &g->csc_w, csc_w, E, ea, device_ptrs, st))) return r;
         if ((r = validate_device(g, g->csc_off, g->csc_row, st, ids_checked))) return r;
-    } else if (!renumber && (r = transpose_csr(g, st))) {
+    } else if (!renumber && (r = build_in_offsets(g, st))) {
         return r;
     }
-    if (csr_w && !g->csc_w && !(renumber && !csc_off)) return IP_E_INVAL;
+    if (csr_w && csc_off && !g->csc_w) return IP_E_INVAL;
 
     // per-vertex arrays
     const size_t nv = (size_t)n;
@@ -889,11 +914,14 @@ static int relabel(ip_graph* g, cudaStream_t st) {
         free_dev(start_old);
         free_dev(chunk_src);
         g->device_bytes -= (size_t)nblk * RL_KEYS * 8 + (size_t)n * 4 + (size_t)n_chunks * 4;
-        if (!alias && g->csc_off) {  // (creation with renumbering may not have built it yet)
+        if (!alias && g->csc_off) {  // (creation with renumbering has not built it yet)
             free_dev(g->csc_off);
+            g->device_bytes -= ((size_t)n + 1) * 4;
+        }
+        if (!alias && g->csc_row) {  // (nor, before a run needs them, the rows)
             free_dev(g->csc_row);
             free_dev(g->csc_w);
-            g->device_bytes -= ((size_t)n + 1) * 4 + ea * 4 * (g->csc_w ? 2 : 1);
+            g->device_bytes -= ea * 4 * (g->csc_w ? 2 : 1);
         }
         free_dev(g->csr_off);
         free_dev(g->csr_col);
@@ -912,11 +940,12 @@ static int relabel(ip_graph* g, cudaStream_t st) {
     g->csr_col = col_new;
     g->csr_w = w_new;
     g->csc_off = g->csc_row = g->csc_w = nullptr;
+    g->csc_rows_pending = false;
     if (alias) {
         g->csc_off = g->csr_off;
         g->csc_row = g->csr_col;
         g->csc_w = g->csr_w;
-    } else if ((r = transpose_csr(g, st))) {
+    } else if ((r = build_in_offsets(g, st))) {
         return r;
     }
     k_degrees<<<grid_for(g, n), 256, 0, st>>>(g->csr_off, n, g->inv_outdeg, &g->ctl->err);
@@ -1034,8 +1063,10 @@ int ip_graph_info(const ip_graph_t* g, ip_graph_info_t* info) {
     info->device_bytes = g->device_bytes;
     // the parts, from the sizes create(), ensure_bins(), ip_graph_relabel() and pb.cu allocate
     const uint64_t nv = g->V, ea = edge_alloc_count(g->E);
-    const uint64_t one_dir = (nv + 1) * 4 + ea * 4 * (g->weighted ? 2 : 1);
-    info->bytes_graph = g->csr_off ? one_dir * (g->csc_alias ? 1 : 2) : 0;
+    const uint64_t off_b = (nv + 1) * 4, rows_b = ea * 4 * (g->weighted ? 2 : 1);
+    uint64_t gb = g->csr_off ? off_b + rows_b : 0;
+    if (!g->csc_alias) gb += (g->csc_off ? off_b : 0) + (g->csc_row ? rows_b : 0);  // rows: once a run built them
+    info->bytes_graph = gb;
     uint64_t vs = 13 * nv * 4 + 3 * (uint64_t)g->W * 4;  // 13 vertex arrays, recv + 2 broadcast bitmaps
     vs += 2 * (uint64_t)(g->hq_cap + 1) * sizeof(uint2);
     if (g->snap_value) vs += nv * 8;

@@ -222,6 +222,7 @@ struct ip_graph {
     uint32_t* csc_row = nullptr;
     uint32_t* csc_w = nullptr;
     bool csc_alias = false;
+    bool csc_rows_pending = false;  // csc_off built, csc_row / csc_w not yet (directed graphs)
     bool weighted = false;
     uint32_t max_out_deg = 0, max_in_deg = 0;
     float* inv_outdeg = nullptr;
@@ -271,6 +272,7 @@ namespace ipg {
 int alloc_dev(ip_graph* g, void** p, size_t bytes);
 void free_dev(void* p);
 int ensure_bins(ip_graph* g, uint32_t t1, uint32_t t2, cudaStream_t st);
+int ensure_in_rows(ip_graph* g, cudaStream_t st);  // the transposed rows, if creation deferred them
 int exclusive_scan(ip_graph* g, uint32_t* data, uint64_t n, cudaStream_t st);  // in place, n uint32
 int cuda_err(cudaError_t e);
 // batch.cu

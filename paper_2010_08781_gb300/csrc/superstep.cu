@@ -761,7 +761,7 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     P.damping = o.damping;
     P.pr_base = (float)((1.0 - (double)o.damping) / (double)g->V);
     P.pr_tol = app == APP_PR ? o.pr_tolerance : 0.f;
-    P.pull_early_exit = (ops && !g->csc_w && o.pull_early_exit) ? 1u : 0u;  // used by programs that allow it
+    P.pull_early_exit = (ops && !g->weighted && o.pull_early_exit) ? 1u : 0u;  // used by programs that allow it
     P.policy = o.policy == IP_POLICY_AUTO ? (g->has_selector ? IP_POLICY_MLP : IP_POLICY_THRESHOLD) : o.policy;
     P.forced_mode = o.forced_mode;
     P.seq_len = o.policy == IP_POLICY_SEQUENCE ? o.mode_sequence_len : 1;
@@ -790,6 +790,14 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
             if (r != IP_OK && !(r == IP_E_RANGE && o.pr_engine == IP_PR_ENGINE_AUTO)) return r;
             if (P.pb.on) CKR(pb_set_mode(g, 1, st));
         }
+    }
+
+    // the in-edge rows (built now if creation deferred them), unless every pull of this
+    // run streams the blocked layout: PageRank with the layout reads none
+    if (!(app == APP_PR && P.pb.on)) {
+        CKR(ensure_in_rows(g, st));
+        P.csc_row = g->csc_row;
+        P.csc_w = g->csc_w;
     }
 
     if (stats && stats->mode_ms && stats->capacity) memset(stats->mode_ms, 0, sizeof(float) * 3 * stats->capacity);

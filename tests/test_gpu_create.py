@@ -68,3 +68,34 @@ def test_pinned_inputs_are_checked(offset):
     with ipg.Graph(g.n, _pin(g.row_ptr, offset), _pin(g.col, offset), symmetric=True) as G:  # and then a good one
         G.run("hashmin")
         assert np.array_equal(G.values("hashmin"), oracle.hashmin(g.n, g.row_ptr, g.col)[0])
+
+
+@pytest.mark.parametrize("relabel", [False, True])
+def test_in_edge_rows_wait_for_the_first_run_that_reads_them(relabel):
+    """A directed graph created without a CSC holds the transpose's offsets only. The
+    blocked PageRank pull streams its own layout and leaves it so; the first run
+    that reads in-edge rows (a pull of SSSP, the gather PageRank engine, a batched
+    run) builds them, weights included, and every result matches the oracle."""
+    d = inputs.rmat_graph(12, weighted=True, seed=6)
+    ea = ((d.m + 3) // 4) * 4 + 4
+    pr, _ = oracle.pagerank(d.n, d.row_ptr, d.col, T=30)
+    srcs = [0, 5, 77]
+    ss = [oracle.sssp(d.n, d.row_ptr, d.col, d.w, source=s)[0] for s in srcs]
+    with ipg.Graph(d.n, d.row_ptr, d.col, d.w, relabel=relabel) as G:
+        csr = (d.n + 1) * 4 + 2 * ea * 4
+        assert G.info()["bytes_graph"] == csr + (d.n + 1) * 4
+        G.run("pagerank", policy="forced", forced_mode="pull", pr_engine="blocked")
+        got = G.values("pagerank").astype(np.float64)
+        assert float(np.max(np.abs(got - pr) / pr)) <= 1e-5
+        assert G.info()["bytes_graph"] == csr + (d.n + 1) * 4
+        G.run("sssp", source=srcs[0], policy="forced", forced_mode="pull")
+        assert np.array_equal(G.values("sssp"), ss[0])
+        assert G.info()["bytes_graph"] == 2 * csr
+        G.run("pagerank", policy="forced", forced_mode="pull", pr_engine="gather")
+        got = G.values("pagerank").astype(np.float64)
+        assert float(np.max(np.abs(got - pr) / pr)) <= 1e-5
+    with ipg.Graph(d.n, d.row_ptr, d.col, d.w, relabel=relabel) as G:  # a batched run first
+        dist, _ = G.run_batch_sssp(srcs)
+        for i in range(len(srcs)):
+            assert np.array_equal(dist[i], ss[i]), i
+        assert G.info()["bytes_graph"] == 2 * csr

@@ -63,7 +63,8 @@ def test_memory_footprint_breakdown():
     with ipg.Graph(d.n, d.row_ptr, d.col, relabel=True) as G:
         i0 = G.info()
         n, ea = d.n, ((d.m + 3) // 4) * 4 + 4
-        assert i0["bytes_graph"] == 2 * ((n + 1) * 4 + ea * 4)  # CSR and device-built CSC, unweighted
+        # CSR and the device-built transpose's offsets: its rows wait for a run that reads them
+        assert i0["bytes_graph"] == 2 * (n + 1) * 4 + ea * 4
         words = ((n + 31) // 32 + 31) // 32 * 32
         assert i0["bytes_vertex_state"] >= 13 * n * 4 + 3 * words * 4
         assert i0["bytes_renumbering"] == 8 * n
@@ -71,7 +72,11 @@ def test_memory_footprint_breakdown():
         G.run("pagerank", policy="forced", forced_mode="pull", pr_engine="blocked")
         i1 = G.info()
         assert i1["bytes_blocked_layout"] >= 8 * d.m  # about 8 bytes per edge
-        for info in (i0, i1):
+        assert i1["bytes_graph"] == i0["bytes_graph"]  # the blocked pull reads no in-edge rows
+        G.run("hashmin", policy="forced", forced_mode="pull")
+        i2 = G.info()
+        assert i2["bytes_graph"] == 2 * ((n + 1) * 4 + ea * 4)  # the gather pull built them
+        for info in (i0, i1, i2):
             parts = sum(info[k] for k in info if k.startswith("bytes_"))
             assert parts == info["device_bytes"]
             assert info["bytes_other"] < 1 << 23  # run log (up to 65,536 supersteps), selector, control
