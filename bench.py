@@ -524,15 +524,20 @@ def run_gpu(args, rank, world, local_rank):
 
 
 def policy_times(G, app, stream, ipg, reps=3):
-    pol = {}
+    """Best of reps whole-run times per policy, and the modes the two selectors chose."""
+    pol, modes = {}, {}
     for name, o in (("threshold", dict(policy="threshold")), ("mlp", dict(policy="mlp")),
                     ("pull", dict(policy="forced", forced_mode="pull")),
                     ("push_dense", dict(policy="forced", forced_mode="push_dense")),
                     ("push_sparse", dict(policy="forced", forced_mode="push_sparse"))):
         try:
-            pol[name] = round(min(G.run(app, stream=stream, **o).elapsed_ms for _ in range(reps)), 4)
+            rs = [G.run(app, stream=stream, **o) for _ in range(reps)]
+            pol[name] = round(min(r.elapsed_ms for r in rs), 4)
+            if name in ("threshold", "mlp"):
+                modes[name] = rs[0].mode[1:].tolist()
         except ipg.IPError:
             pol[name] = None
+    pol["modes"] = modes
     return pol
 
 

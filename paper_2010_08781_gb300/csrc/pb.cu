@@ -588,38 +588,73 @@ __global__ void k_pb_tails(uint32_t* code, const uint2* tails, uint32_t nb, uint
 }
 
 // ---------------------------------------------------------------- layout build
-__global__ void k_pb_binof(const uint32_t* __restrict__ bstart, uint32_t* binof) {
-    const uint32_t q = blockIdx.x;
-    for (uint32_t v = bstart[q] + threadIdx.x; v < bstart[q + 1]; v += blockDim.x) binof[v] = q;
+// Bin of a destination without a per-vertex table: tab[b] is the bin of vertex
+// min(b << sh, V - 1) (at most PB_TAB + 1 entries, in shared memory), so the bin of v
+// lies in [tab[v >> sh], tab[(v >> sh) + 1]]; a binary search over the bin starts
+// (global, L1-resident) narrows that range, which holds one or two bins except where
+// the bins are narrow (the high in-degree vertices).
+constexpr uint32_t PB_TAB = 4096;
+__device__ __forceinline__ uint32_t pb_bin_of(uint32_t v, const uint32_t* tab, uint32_t sh,
+                                              const uint32_t* __restrict__ bstart) {
+    const uint32_t b = v >> sh;
+    uint32_t lo = tab[b], hi = tab[b + 1];
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(bstart + mid) <= v)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
 }
 
-// Entries per bin of one chunk, in shared memory.
-__device__ __forceinline__ void pb_hist(const uint32_t* __restrict__ col, const uint32_t* __restrict__ binof,
-                                        uint32_t e0, uint32_t e1, uint32_t nb, uint32_t* hist) {
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) atomicAdd(hist + binof[col[e]], 1u);
-    __syncthreads();
+__global__ void k_pb_tab(const uint32_t* __restrict__ bstart, uint32_t nb, uint32_t V, uint32_t sh, uint32_t ntab,
+                         uint32_t* tab) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= ntab; i += gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)min((uint64_t)i << sh, (uint64_t)V - 1);
+        uint32_t lo = 0, hi = nb - 1;  // the last bin whose start is <= x
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (bstart[mid] <= x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        tab[i] = lo;
+    }
+}
+
+__device__ __forceinline__ void pb_load_tab(const uint32_t* __restrict__ g_tab, uint32_t ntab, uint32_t* tab) {
+    for (uint32_t i = threadIdx.x; i <= ntab; i += blockDim.x) tab[i] = g_tab[i];
 }
 
 __device__ __forceinline__ uint32_t pad4(uint32_t n) { return (n + 3) & ~3u; }
 
-// Per chunk: its row of the chunk x bin matrix of run lengths padded to 4
-// entries, its number of runs and its padded entry count.
+// Per chunk: its entries per bin (row c of the chunk x bin matrix of run lengths),
+// its number of runs and its padded entry count.
 __global__ void __launch_bounds__(PBB_THREADS) k_pb_count(const uint32_t* __restrict__ csr_off,
                                                           const uint32_t* __restrict__ col,
                                                           const uint4* __restrict__ cs,
-                                                          const uint32_t* __restrict__ binof, uint32_t nb,
-                                                          uint32_t* M, uint32_t* chunk_runs, uint32_t* chunk_len) {
-    extern __shared__ uint32_t hist[];
+                                                          const uint32_t* __restrict__ g_tab, uint32_t sh,
+                                                          uint32_t ntab, const uint32_t* __restrict__ bstart,
+                                                          uint32_t nb, uint32_t* M, uint32_t* chunk_runs,
+                                                          uint32_t* chunk_len) {
+    extern __shared__ uint32_t sm[];
+    uint32_t* hist = sm;       // [nb]
+    uint32_t* tab = sm + nb;   // [ntab + 1]
     const uint32_t c = blockIdx.x;
-    pb_hist(col, binof, csr_off[cs[c].x], csr_off[cs[c].x + cs[c].y], nb, hist);
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    pb_load_tab(g_tab, ntab, tab);
+    __syncthreads();
+    const uint32_t e0 = csr_off[cs[c].x], e1 = csr_off[cs[c].x + cs[c].y];
+    for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) atomicAdd(hist + pb_bin_of(col[e], tab, sh, bstart), 1u);
+    __syncthreads();
     uint32_t runs = 0, len = 0;
     for (uint32_t q = threadIdx.x; q < nb; q += blockDim.x) {
-        const uint32_t n4 = pad4(hist[q]);
-        M[(size_t)c * nb + q] = n4;
-        runs += n4 ? 1u : 0u;
-        len += n4;
+        const uint32_t n = hist[q];
+        M[(size_t)c * nb + q] = n;
+        runs += n ? 1u : 0u;
+        len += pad4(n);
     }
     for (int o = 16; o; o >>= 1) {
         runs += __shfl_xor_sync(FULL, runs, o);
@@ -631,43 +666,55 @@ __global__ void __launch_bounds__(PBB_THREADS) k_pb_count(const uint32_t* __rest
     }
 }
 
-// Per bin: exclusive scan of its column over the chunks (the place of every
-// padded run inside its bin), and the bin's padded total.
-__global__ void k_pb_colscan(uint32_t* M, uint32_t nC, uint32_t nb, uint32_t* total) {
+// Per bin: exclusive scan of its column of padded run lengths over the chunks (the
+// place of every run inside its bin, into O), and the bin's padded total.
+__global__ void k_pb_colscan(const uint32_t* __restrict__ M, uint32_t* O, uint32_t nC, uint32_t nb, uint32_t* total) {
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nb) return;
     uint32_t run = 0;
     for (uint32_t c = 0; c < nC; ++c) {
-        const uint32_t t = M[(size_t)c * nb + q];
-        M[(size_t)c * nb + q] = run;
+        const uint32_t t = pad4(M[(size_t)c * nb + q]);
+        O[(size_t)c * nb + q] = run;
         run += t;
     }
     total[q] = run;
 }
 
-// Per chunk: the run records (padded to 4 entries, the padding reads source
-// `ns` whose code is 0), then every out-edge into its run in both orders.
+constexpr uint32_t PB_PIECE = 1024;  // out-edges per warp task of k_pb_place
+
+// Per chunk: the run records (padded to 4 entries, the padding reads source `ns`
+// whose code is the neutral one), then every out-edge into its run in both orders.
+// The out-edges are taken by warps in pieces of PB_PIECE; a warp keeps the offsets
+// of 32 consecutive sources in registers and finds each lane's source by a 5-step
+// shuffle search (the sources' edge ranges are sorted), sliding the window forward
+// as the piece advances.
 __global__ void __launch_bounds__(PBB_THREADS) k_pb_place(const uint32_t* __restrict__ csr_off,
                                                           const uint32_t* __restrict__ col,
                                                           const uint4* __restrict__ cs,
                                                           const uint32_t* __restrict__ abase,
-                                                          const uint32_t* __restrict__ binof,
-                                                          const uint32_t* __restrict__ bstart,
+                                                          const uint32_t* __restrict__ g_tab, uint32_t sh,
+                                                          uint32_t ntab, const uint32_t* __restrict__ bstart,
                                                           const uint32_t* __restrict__ bbase, uint32_t nb,
-                                                          const uint32_t* __restrict__ M, uint4* runs,
+                                                          const uint32_t* __restrict__ M,
+                                                          const uint32_t* __restrict__ O, uint4* runs,
                                                           uint16_t* src, uint16_t* dst) {
     extern __shared__ uint32_t sm[];
-    uint32_t* cnt = sm;             // [nb]: entries per bin, then the run's offset inside the chunk
-    uint32_t* cur = sm + nb;        // [nb]: placement cursor
-    uint32_t* offs = sm + 2 * nb;   // [ns + 1]: the chunk's CSR offsets
+    uint32_t* cnt = sm;            // [nb]: entries per bin, then the run's offset inside the chunk
+    uint32_t* cur = sm + nb;       // [nb]: placement cursor
+    uint32_t* rb = sm + 2 * nb;    // [nb]: the run's bin-major start
+    uint32_t* tab = sm + 3 * nb;   // [ntab + 1]
     __shared__ uint32_t wsum[PBB_THREADS / 32], wnz[PBB_THREADS / 32];
     const uint4 ch = cs[blockIdx.x];
     const uint32_t s0 = ch.x, ns = ch.y, a_c = abase[blockIdx.x];
     const uint32_t* Mc = M + (size_t)blockIdx.x * nb;
-    for (uint32_t i = threadIdx.x; i <= ns; i += blockDim.x) offs[i] = csr_off[s0 + i];
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = 0;
-    pb_hist(col, binof, csr_off[s0], csr_off[s0 + ns], nb, cnt);
-    const uint32_t e0 = offs[0], e1 = offs[ns];
+    const uint32_t* Oc = O + (size_t)blockIdx.x * nb;
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
+        cnt[i] = Mc[i];
+        cur[i] = 0;
+        rb[i] = bbase[i] + Oc[i];
+    }
+    pb_load_tab(g_tab, ntab, tab);
+    __syncthreads();
     // exclusive scans of the padded counts and of the non-empty bins: thread t owns bins [b0, b1)
     const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
     const uint32_t b0 = min(nb, threadIdx.x * per), b1 = min(nb, b0 + per);
@@ -698,29 +745,58 @@ __global__ void __launch_bounds__(PBB_THREADS) k_pb_place(const uint32_t* __rest
     for (uint32_t q = b0; q < b1; ++q) {
         const uint32_t n = cnt[q], n4 = pad4(n);
         if (n) {
-            runs[ch.z + rk++] = make_uint4(a_c + off, bbase[q] + Mc[q], n4, 0u);
+            runs[ch.z + rk++] = make_uint4(a_c + off, rb[q], n4, 0u);
             for (uint32_t k = n; k < n4; ++k) {
                 src[a_c + off + k] = (uint16_t)ns;
-                dst[bbase[q] + Mc[q] + k] = 0;
+                dst[rb[q] + k] = 0;
             }
         }
         cnt[q] = off;
         off += n4;
     }
     __syncthreads();
-    for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const uint32_t v = col[e], q = binof[v];
-        uint32_t lo = 0, hi = ns;  // offs[lo] <= e < offs[hi]
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (offs[mid] <= e)
+    const uint32_t* offs = csr_off + s0;  // the chunk's offsets, ns + 1 of them
+    const uint32_t e0 = offs[0], e1 = offs[ns];
+    const uint32_t n_pieces = (e1 - e0 + PB_PIECE - 1) / PB_PIECE;
+    for (uint32_t piece = w; piece < n_pieces; piece += blockDim.x / 32) {
+        const uint32_t p0 = e0 + piece * PB_PIECE, p1 = min(e1, p0 + PB_PIECE);
+        // the window starts at the source of p0: the last s with offs[s] <= p0
+        uint32_t lo = 0, hi = ns - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (offs[mid] <= p0)
                 lo = mid;
             else
-                hi = mid;
+                hi = mid - 1;
         }
-        const uint32_t k = atomicAdd(cur + q, 1u);
-        src[a_c + cnt[q] + k] = (uint16_t)lo;
-        dst[bbase[q] + Mc[q] + k] = (uint16_t)(v - bstart[q]);
+        uint32_t ws = lo;                              // first source of the window
+        uint32_t a = offs[min(ws + lane, ns)];         // lane i: first edge of source ws + i
+        uint32_t wend = offs[min(ws + 32, ns)];        // first edge after the window
+        for (uint32_t base = p0; base < p1; base += 32) {
+            const uint32_t e = base + lane;
+            bool pending = e < p1;
+            while (__any_sync(FULL, pending)) {  // warp-uniform: every lane takes part in the shuffles
+                uint32_t j = 0;                     // the last lane j with a_j <= e
+#pragma unroll
+                for (uint32_t k = 16; k; k >>= 1) {
+                    const uint32_t aj = __shfl_sync(FULL, a, j + k);
+                    if (aj <= e) j += k;
+                }
+                if (pending && e < wend) {
+                    const uint32_t v = col[e];
+                    const uint32_t q = pb_bin_of(v, tab, sh, bstart);
+                    const uint32_t k = atomicAdd(cur + q, 1u);
+                    src[a_c + cnt[q] + k] = (uint16_t)(ws + j);
+                    dst[rb[q] + k] = (uint16_t)(v - __ldg(bstart + q));
+                    pending = false;
+                }
+                if (__any_sync(FULL, pending)) {  // some lane's edge lies past the window: slide it
+                    ws = min(ws + 32, ns - 1);
+                    a = offs[min(ws + lane, ns)];
+                    wend = offs[min(ws + 32, ns)];
+                }
+            }
+        }
     }
 }
 
@@ -899,11 +975,16 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     uint4* d_cs;
     uint32_t* d_bstart;
     PBK(pb_alloc(g, L, &d_cs, nC));
-    TmpBuf t_binof{g}, t_bstart{g}, t_M{g}, t_chunk_runs{g}, t_chunk_len{g}, t_total{g}, t_bbase{g}, t_abase{g};
-    uint32_t *d_binof, *d_M, *d_chunk_runs, *d_chunk_len, *d_total, *d_bbase, *d_abase;
-    PBK(t_binof.alloc(&d_binof, V));
+    // the bin lookup table: ntab + 1 entries, vertex blocks of 2^sh
+    uint32_t sh = 0;
+    while (((V - 1) >> sh) + 1 > PB_TAB) ++sh;
+    const uint32_t ntab = ((V - 1) >> sh) + 1;
+    TmpBuf t_tab{g}, t_bstart{g}, t_M{g}, t_O{g}, t_chunk_runs{g}, t_chunk_len{g}, t_total{g}, t_bbase{g}, t_abase{g};
+    uint32_t *d_tab, *d_M, *d_O, *d_chunk_runs, *d_chunk_len, *d_total, *d_bbase, *d_abase;
+    PBK(t_tab.alloc(&d_tab, ntab + 1));
     PBK(t_bstart.alloc(&d_bstart, nb + 1));
     PBK(t_M.alloc(&d_M, (size_t)nC * nb));
+    PBK(t_O.alloc(&d_O, (size_t)nC * nb));
     PBK(t_chunk_runs.alloc(&d_chunk_runs, nC));
     PBK(t_chunk_len.alloc(&d_chunk_len, nC));
     PBK(t_abase.alloc(&d_abase, nC));
@@ -915,15 +996,15 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     PBK(cuda_err(cudaMemcpyAsync(d_bstart, bstart.data(), sizeof(uint32_t) * (nb + 1), cudaMemcpyHostToDevice, st)));
     PBK(cuda_err(cudaMemsetAsync(d_chunk_runs, 0, sizeof(uint32_t) * std::max<uint32_t>(nC, 1), st)));
     PBK(cuda_err(cudaMemsetAsync(d_chunk_len, 0, sizeof(uint32_t) * std::max<uint32_t>(nC, 1), st)));
-    k_pb_binof<<<nb, 256, 0, st>>>(d_bstart, d_binof);
-    const size_t smem_count = sizeof(uint32_t) * nb;
-    const size_t smem_place = sizeof(uint32_t) * (2 * nb + PB_MAXS + 1);
+    k_pb_tab<<<(ntab + 256) / 256, 256, 0, st>>>(d_bstart, nb, V, sh, ntab, d_tab);
+    const size_t smem_count = sizeof(uint32_t) * (nb + ntab + 1);
+    const size_t smem_place = sizeof(uint32_t) * (3 * nb + ntab + 1);
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_count)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place)));
     if (nC) {
-        k_pb_count<<<nC, PBB_THREADS, smem_count, st>>>(g->csr_off, g->csr_col, d_cs, d_binof, nb, d_M,
-                                                        d_chunk_runs, d_chunk_len);
-        k_pb_colscan<<<(nb + 255) / 256, 256, 0, st>>>(d_M, nC, nb, d_total);
+        k_pb_count<<<nC, PBB_THREADS, smem_count, st>>>(g->csr_off, g->csr_col, d_cs, d_tab, sh, ntab, d_bstart,
+                                                        nb, d_M, d_chunk_runs, d_chunk_len);
+        k_pb_colscan<<<(nb + 255) / 256, 256, 0, st>>>(d_M, d_O, nC, nb, d_total);
     } else {
         PBK(cuda_err(cudaMemsetAsync(d_total, 0, sizeof(uint32_t) * nb, st)));
     }
@@ -972,8 +1053,8 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     PBK(cuda_err(cudaMemsetAsync(d_dst, 0, sizeof(uint16_t) * std::max<uint64_t>(P_total, 1), st)));
     PBK(cuda_err(cudaMemsetAsync(d_code, 0, sizeof(uint32_t) * std::max<uint64_t>(P_total, 1), st)));
     if (nC)
-        k_pb_place<<<nC, PBB_THREADS, smem_place, st>>>(g->csr_off, g->csr_col, d_cs, d_abase, d_binof, d_bstart,
-                                                        d_bbase, nb, d_M, d_runs, d_src, d_dst);
+        k_pb_place<<<nC, PBB_THREADS, smem_place, st>>>(g->csr_off, g->csr_col, d_cs, d_abase, d_tab, sh, ntab,
+                                                        d_bstart, d_bbase, nb, d_M, d_O, d_runs, d_src, d_dst);
     PBK(cuda_err(cudaGetLastError()));
 
     // phase-2 tasks, one per bin, in bin order; the tail of every bin (entries after its runs)

@@ -236,24 +236,39 @@ __global__ void __launch_bounds__(BLOCK) k_pr_apply(Params P) {
 __device__ __forceinline__ float bf16f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
 // One warp: 8 -> 32 -> 32 -> 3 MLP, BF16 weights, FP32 accumulation. Lane j owns
-// hidden unit j of both layers. All of a lane's parameters are loaded at once at
-// the start (its W1 row as one 16-byte load, its W2 row as four, its W3 column,
-// biases, and the feature normalisation by lanes 0-7), so inference waits for one
-// L2 round trip instead of one per layer; the arithmetic and its order are those
-// of the training forward pass (ip_mlp_forward), so the logits are identical.
+// hidden unit j of both layers. A lane's parameters (its W1 row as one 16-byte
+// load, its W2 row as four, its W3 column, biases, and the feature normalisation
+// by lanes 0-7) are loaded by mlp_load at the start of k_select, so their L2 round
+// trip overlaps the one for the superstep's counters; the arithmetic and its order
+// are those of the training forward pass (ip_mlp_forward), so the logits are
+// identical.
 static_assert(offsetof(SelectorDev, W1) % 16 == 0 && offsetof(SelectorDev, W2) % 16 == 0, "16-byte weight rows");
-__device__ int mlp_mode(const SelectorDev* S, const float* f) {
-    const uint32_t j = lane_id();
-    const uint4 w1 = __ldg(reinterpret_cast<const uint4*>(S->W1) + j);  // W1[j][0..7]
+struct MlpLane {
+    uint4 w1;
     uint4 w2[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) w2[q] = __ldg(reinterpret_cast<const uint4*>(S->W2 + j * 32) + q);  // W2[j][8q..8q+7]
-    const float b1 = __ldg(S->b1 + j), b2 = __ldg(S->b2 + j);
+    float b1, b2, b3m, mu, sd;
     uint16_t w3[3];
+};
+__device__ __forceinline__ MlpLane mlp_load(const SelectorDev* S) {
+    const uint32_t j = lane_id();
+    MlpLane L;
+    L.w1 = __ldg(reinterpret_cast<const uint4*>(S->W1) + j);  // W1[j][0..7]
 #pragma unroll
-    for (int m = 0; m < 3; ++m) w3[m] = __ldg(S->W3 + m * 32 + j);
-    const float b3m = j < 3 ? __ldg(S->b3 + j) : 0.f;
-    const float mu = j < 8 ? __ldg(S->mu + j) : 0.f, sd = j < 8 ? __ldg(S->sd + j) : 1.f;
+    for (int q = 0; q < 4; ++q) L.w2[q] = __ldg(reinterpret_cast<const uint4*>(S->W2 + j * 32) + q);  // W2[j][8q..]
+    L.b1 = __ldg(S->b1 + j);
+    L.b2 = __ldg(S->b2 + j);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) L.w3[m] = __ldg(S->W3 + m * 32 + j);
+    L.b3m = j < 3 ? __ldg(S->b3 + j) : 0.f;
+    L.mu = j < 8 ? __ldg(S->mu + j) : 0.f;
+    L.sd = j < 8 ? __ldg(S->sd + j) : 1.f;
+    return L;
+}
+__device__ int mlp_mode(const MlpLane& L, const float* f) {
+    const uint4 w1 = L.w1;
+    const uint4* w2 = L.w2;
+    const float b1 = L.b1, b2 = L.b2, b3m = L.b3m, mu = L.mu, sd = L.sd;
+    const uint16_t* w3 = L.w3;
     float xn[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) xn[i] = (f[i] - __shfl_sync(FULL, mu, i)) / __shfl_sync(FULL, sd, i);
@@ -290,6 +305,8 @@ __device__ int mlp_mode(const SelectorDev* S, const float* f) {
 __global__ void k_stamp(DevCtl* c) { c->t_prev = globaltimer(); }
 
 __global__ void k_select(Params P) {
+    MlpLane mlp{};
+    if (P.policy == IP_POLICY_MLP) mlp = mlp_load(P.sel);  // in flight while the counters load
     DevCtl* c = P.ctl;
     const uint32_t s = c->superstep;
     uint32_t act, bc, maxd;
@@ -329,7 +346,7 @@ __global__ void k_select(Params P) {
         case IP_POLICY_FORCED: mode = P.forced_mode; break;
         case IP_POLICY_SEQUENCE: mode = P.seq[s % P.seq_len]; break;
         case IP_POLICY_MLP:  // below the sparse cutoff every policy takes push-sparse: no inference there
-            mode = f[6] < P.thr_sparse ? IP_MODE_PUSH_SPARSE : mlp_mode(P.sel, f);
+            mode = f[6] < P.thr_sparse ? IP_MODE_PUSH_SPARSE : mlp_mode(mlp, f);
             break;
         default:
             mode = f[6] < P.thr_sparse ? IP_MODE_PUSH_SPARSE : (f[6] >= P.thr_pull ? IP_MODE_PULL : IP_MODE_PUSH_DENSE);
