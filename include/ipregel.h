@@ -69,7 +69,8 @@ typedef enum {
 typedef enum { IP_MODE_PUSH_SPARSE = 0, IP_MODE_PUSH_DENSE = 1, IP_MODE_PULL = 2 } ip_mode_t;
 
 typedef enum {
-    IP_POLICY_AUTO = 0,      /* the learned selector if one is loaded, else the threshold rule */
+    IP_POLICY_AUTO = 0,      /* the threshold rule (the learned selector is IP_POLICY_MLP: it gains
+                                on some graph shapes and loses 0.2-1.7% on R-MAT 22 and 26) */
     IP_POLICY_THRESHOLD = 1, /* fixed rule on the frontier's out-edge fraction (see ip_options_t) */
     IP_POLICY_MLP = 2,       /* the learned selector; IP_E_STATE if none is loaded. A superstep whose
                                 frontier sends fewer than thr_sparse * E messages takes PUSH_SPARSE

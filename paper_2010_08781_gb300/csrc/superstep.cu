@@ -779,7 +779,9 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     P.pr_base = (float)((1.0 - (double)o.damping) / (double)g->V);
     P.pr_tol = app == APP_PR ? o.pr_tolerance : 0.f;
     P.pull_early_exit = (ops && !g->weighted && o.pull_early_exit) ? 1u : 0u;  // used by programs that allow it
-    P.policy = o.policy == IP_POLICY_AUTO ? (g->has_selector ? IP_POLICY_MLP : IP_POLICY_THRESHOLD) : o.policy;
+    // AUTO is the threshold rule: on R-MAT 22 and 26 graphs the learned selector picks the
+    // same modes or slightly slower ones, and its inference costs a few microseconds
+    P.policy = o.policy == IP_POLICY_AUTO ? IP_POLICY_THRESHOLD : o.policy;
     P.forced_mode = o.forced_mode;
     P.seq_len = o.policy == IP_POLICY_SEQUENCE ? o.mode_sequence_len : 1;
     if (o.policy == IP_POLICY_SEQUENCE) memcpy(P.seq, o.mode_sequence, o.mode_sequence_len);
