@@ -10,7 +10,8 @@ global halt.
 
 Metric: GTEPS = edges traversed by messages (PageRank: E per broadcasting
 superstep, T·E per run; Hashmin: the out-degrees of the broadcasting vertices,
-summed over supersteps) / step time. The JSON line also carries the roofline of
+summed over supersteps) / step time; per app, gteps_graph500 is the graph's edge
+count over the run time. The JSON line also carries the roofline of
 the dominant kernel (the blocked pull's two launches per superstep: 8E + 20V
 algorithmic bytes over their CUDA-event time, against the measured HBM copy
 bandwidth), the end-to-end number through the C ABI from pinned host buffers,
@@ -19,7 +20,7 @@ secondary configurations (Hashmin + SSSP on symmetrised R-MAT 22, PageRank on
 R-MAT 16) are reported under per_app.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-  python bench.py --config c2|c1|c4        secondary configurations, one line each
+  python bench.py --config c2|c1|c4|bfs_perm   secondary configurations, one line each
   python bench.py --ncu-case APP:MODE[:ENGINE] --scale S   small profiling case
 """
 from __future__ import annotations
@@ -456,7 +457,8 @@ def run_gpu(args, rank, world, local_rank):
     gather = min(P.run("pagerank", pr_engine="gather", **pr_kw).elapsed_ms for _ in range(2))
     detail["pagerank"]["gather_engine_ms"] = round(gather, 3)
     hmsg = int(runs["hashmin"][0].messages.sum())
-    detail["hashmin"] = {"gteps": round(hmsg / (hm_ms * 1e-3) / 1e9, 2), "ms": round(hm_ms, 3),
+    detail["hashmin"] = {"gteps": round(hmsg / (hm_ms * 1e-3) / 1e9, 2),
+                         "gteps_graph500": round(Es / (hm_ms * 1e-3) / 1e9, 2), "ms": round(hm_ms, 3),
                          "supersteps": runs["hashmin"][0].supersteps, "messages": hmsg, "edges": Es,
                          "modes": runs["hashmin"][0].mode[1:].tolist(),
                          "policy_ms": policy_times(H, "hashmin", stream, ipg)}
@@ -549,7 +551,8 @@ def c2_summary(args, stream, ipg, steps=10):
             rs = [G.run(app, policy=args.policy, stream=stream, **kw) for _ in range(steps + 2)][2:]
             ms = statistics.median(r.elapsed_ms for r in rs)
             m = int(rs[0].messages.sum())
-            out[app] = {"gteps": round(m / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 4), "supersteps": rs[0].supersteps,
+            out[app] = {"gteps": round(m / (ms * 1e-3) / 1e9, 2), "gteps_graph500": round(g.m / (ms * 1e-3) / 1e9, 2),
+                        "ms": round(ms, 4), "supersteps": rs[0].supersteps,
                         "messages": m, "modes": rs[0].mode[1:].tolist(),
                         "policy_ms": policy_times(G, app, stream, ipg)}
         out["memory"] = memory_report(G, "symmetrised weighted R-MAT 22")
