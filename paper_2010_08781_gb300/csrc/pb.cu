@@ -51,6 +51,12 @@ constexpr uint32_t PB_CHUNK_MIN = 65536, PB_CHUNK_MAX = 262144;  // target out-e
 constexpr uint32_t PB_MAX_BINS = 16384;  // bins a chunk histograms in shared memory
 constexpr uint32_t PB_MAX_V = 13824u * PB_BIN_V;  // vertex-capped bins plus entry-capped ones fit PB_MAX_BINS
 constexpr int PB1_THREADS = 512, PBB_THREADS = 512;
+// k_pb_place: one CTA of 1024 threads per SM (its shared memory is padded to
+// PBP_MIN_SMEM): each CTA writes its chunk's runs, spread over about 0.5 MB, as
+// its edges come; with 152 chunks in flight those writes stay in L2 until their
+// sectors are complete instead of leaving it half written and being read back.
+constexpr int PBP_THREADS = 1024;
+constexpr size_t PBP_MIN_SMEM = 120 * 1024;
 constexpr int PB1_LOADS = 4;         // phase 1: groups of 4 entries per lane in flight
 constexpr int PB_BATCH = 8;          // per-vertex loops (staging, compute()): loads in flight per thread
 constexpr int PB2_CONSUMERS = 24;    // phase 2: consumer warps (plus one producer warp)
@@ -688,7 +694,7 @@ constexpr uint32_t PB_PIECE = 1024;  // out-edges per warp task of k_pb_place
 // of 32 consecutive sources in registers and finds each lane's source by a 5-step
 // shuffle search (the sources' edge ranges are sorted), sliding the window forward
 // as the piece advances.
-__global__ void __launch_bounds__(PBB_THREADS) k_pb_place(const uint32_t* __restrict__ csr_off,
+__global__ void __launch_bounds__(PBP_THREADS, 1) k_pb_place(const uint32_t* __restrict__ csr_off,
                                                           const uint32_t* __restrict__ col,
                                                           const uint4* __restrict__ cs,
                                                           const uint32_t* __restrict__ abase,
@@ -703,7 +709,7 @@ __global__ void __launch_bounds__(PBB_THREADS) k_pb_place(const uint32_t* __rest
     uint32_t* cur = sm + nb;       // [nb]: placement cursor
     uint32_t* rb = sm + 2 * nb;    // [nb]: the run's bin-major start
     uint32_t* tab = sm + 3 * nb;   // [ntab + 1]
-    __shared__ uint32_t wsum[PBB_THREADS / 32], wnz[PBB_THREADS / 32];
+    __shared__ uint32_t wsum[PBP_THREADS / 32], wnz[PBP_THREADS / 32];
     const uint4 ch = cs[blockIdx.x];
     const uint32_t s0 = ch.x, ns = ch.y, a_c = abase[blockIdx.x];
     const uint32_t* Mc = M + (size_t)blockIdx.x * nb;
@@ -805,8 +811,11 @@ __global__ void __launch_bounds__(PBB_THREADS) k_pb_place(const uint32_t* __rest
 // it has fewer than max_n vertices and at most per_e edges (a vertex with more edges
 // than that is a group of its own). The greedy pass is sequential, but where a group
 // that starts at u ends depends on u alone: k_pb_next finds that end for every u in
-// parallel (a binary search, the offsets being sorted), and k_pb_walk follows the
-// chain of ends from vertex 0, one dependent step per group.
+// parallel (a binary search, the offsets being sorted). The chain of ends from vertex 0
+// is then followed PB_JUMP groups at a time: k_pb_jump gives every u the start of the
+// group PB_JUMP groups later, one thread walks those jumps from vertex 0 (one dependent
+// load per PB_JUMP groups instead of per group: each costs a trip to DRAM), and
+// k_pb_fill expands every jump into its PB_JUMP group starts in parallel.
 __global__ void k_pb_next(const uint32_t* __restrict__ off, uint32_t n, uint32_t per_e, uint32_t max_n,
                           uint32_t* nxt) {
     for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
@@ -826,16 +835,44 @@ __global__ void k_pb_next(const uint32_t* __restrict__ off, uint32_t n, uint32_t
     }
 }
 
-// One thread: the group starts {first vertex, its first edge} in order, at most cap of
-// them (*count = cap + 1 if the chain did not end within cap groups).
-__global__ void k_pb_walk(const uint32_t* __restrict__ nxt, const uint32_t* __restrict__ off, uint32_t n,
-                          uint32_t cap, uint2* starts, uint32_t* count) {
-    uint32_t u = 0, k = 0;
-    while (u < n && k < cap) {
-        starts[k++] = make_uint2(u, off[u]);
-        u = nxt[u];
+constexpr uint32_t PB_JUMP = 16;
+
+__global__ void k_pb_jump(const uint32_t* __restrict__ nxt, uint32_t n, uint32_t* jk) {
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        uint32_t v = u;
+        for (uint32_t i = 0; i < PB_JUMP && v < n; ++i) v = nxt[v];
+        jk[u] = v;
     }
-    *count = u < n ? cap + 1 : k;
+}
+
+// One thread: every PB_JUMP-th group start from vertex 0, at most acap of them
+// (*n_anchors = acap + 1 if the chain goes on). *count starts as "did not end".
+__global__ void k_pb_anchors(const uint32_t* __restrict__ jk, uint32_t n, uint32_t acap, uint32_t cap,
+                             uint32_t* anchors, uint32_t* n_anchors, uint32_t* count) {
+    uint32_t u = 0, k = 0;
+    while (u < n && k < acap) {
+        anchors[k++] = u;
+        u = jk[u];
+    }
+    *n_anchors = u < n ? acap + 1 : k;
+    *count = cap + 1;
+}
+
+// Anchor i's PB_JUMP group starts {first vertex, its first edge} at places i * PB_JUMP
+// on; the walk of the last anchor reaches n and writes the number of groups.
+__global__ void k_pb_fill(const uint32_t* __restrict__ nxt, const uint32_t* __restrict__ off, uint32_t n,
+                          const uint32_t* __restrict__ anchors, const uint32_t* __restrict__ n_anchors,
+                          uint32_t acap, uint32_t cap, uint2* starts, uint32_t* count) {
+    const uint32_t na = min(*n_anchors, acap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < na; i += gridDim.x * blockDim.x) {
+        uint32_t u = anchors[i];
+        uint64_t k = (uint64_t)i * PB_JUMP;
+        for (uint32_t j = 0; j < PB_JUMP && u < n; ++j, ++k) {
+            if (k < cap) starts[k] = make_uint2(u, off[u]);
+            u = nxt[u];
+        }
+        if (u >= n) *count = k <= (uint64_t)cap ? (uint32_t)k : cap + 1;
+    }
 }
 
 // Host-side owner of the layout's device buffers.
@@ -893,15 +930,20 @@ int pb_cuts(ip_graph* g, const uint32_t* off, uint32_t n, uint64_t per_e, uint32
     const uint32_t pe = (uint32_t)std::min<uint64_t>(per_e, 0xFFFFFFFFull);
     const uint64_t bound = (uint64_t)n / max_n + 2 * g->E / pe + 16;
     const uint32_t cap = (uint32_t)std::min<uint64_t>(bound, n);
-    uint32_t *nxt = nullptr, *count = nullptr;
+    const uint32_t acap = cap / PB_JUMP + 2;
+    uint32_t *nxt = nullptr, *count = nullptr, *jk = nullptr, *anchors = nullptr;
     uint2* starts = nullptr;
     int r = alloc_dev(g, (void**)&nxt, (size_t)n * sizeof(uint32_t));
-    if (!r) r = alloc_dev(g, (void**)&count, sizeof(uint32_t));
+    if (!r) r = alloc_dev(g, (void**)&jk, (size_t)n * sizeof(uint32_t));
+    if (!r) r = alloc_dev(g, (void**)&count, 2 * sizeof(uint32_t));
+    if (!r) r = alloc_dev(g, (void**)&anchors, (size_t)acap * sizeof(uint32_t));
     if (!r) r = alloc_dev(g, (void**)&starts, std::max<size_t>(cap, 1) * sizeof(uint2));
     if (!r) {
         const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)g->num_sms * 8, ((uint64_t)n + 255) / 256));
         k_pb_next<<<grid, 256, 0, st>>>(off, n, pe, max_n, nxt);
-        k_pb_walk<<<1, 1, 0, st>>>(nxt, off, n, cap, starts, count);
+        k_pb_jump<<<grid, 256, 0, st>>>(nxt, n, jk);
+        k_pb_anchors<<<1, 1, 0, st>>>(jk, n, acap, cap, anchors, count + 1, count);
+        k_pb_fill<<<(acap + 255) / 256, 256, 0, st>>>(nxt, off, n, anchors, count + 1, acap, cap, starts, count);
         r = cuda_err(cudaGetLastError());
     }
     uint32_t total = 0;
@@ -913,8 +955,9 @@ int pb_cuts(ip_graph* g, const uint32_t* off, uint32_t n, uint64_t per_e, uint32
         r = cuda_err(cudaMemcpyAsync(out->data(), starts, sizeof(uint2) * total, cudaMemcpyDeviceToHost, st));
     }
     if (!r) r = cuda_err(cudaStreamSynchronize(st));
-    for (void* p : {(void*)nxt, (void*)count, (void*)starts}) free_dev(p);
-    g->device_bytes -= (nxt ? (size_t)n * sizeof(uint32_t) : 0) + (count ? sizeof(uint32_t) : 0) +
+    for (void* p : {(void*)nxt, (void*)jk, (void*)count, (void*)anchors, (void*)starts}) free_dev(p);
+    g->device_bytes -= (nxt ? (size_t)n * sizeof(uint32_t) : 0) + (jk ? (size_t)n * sizeof(uint32_t) : 0) +
+                       (count ? 2 * sizeof(uint32_t) : 0) + (anchors ? (size_t)acap * sizeof(uint32_t) : 0) +
                        (starts ? std::max<size_t>(cap, 1) * sizeof(uint2) : 0);
     return r;
 }
@@ -998,7 +1041,7 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     PBK(cuda_err(cudaMemsetAsync(d_chunk_len, 0, sizeof(uint32_t) * std::max<uint32_t>(nC, 1), st)));
     k_pb_tab<<<(ntab + 256) / 256, 256, 0, st>>>(d_bstart, nb, V, sh, ntab, d_tab);
     const size_t smem_count = sizeof(uint32_t) * (nb + ntab + 1);
-    const size_t smem_place = sizeof(uint32_t) * (3 * nb + ntab + 1);
+    const size_t smem_place = std::max(PBP_MIN_SMEM, sizeof(uint32_t) * (3 * nb + ntab + 1));
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_count)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_place)));
     if (nC) {
@@ -1053,7 +1096,7 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     PBK(cuda_err(cudaMemsetAsync(d_dst, 0, sizeof(uint16_t) * std::max<uint64_t>(P_total, 1), st)));
     PBK(cuda_err(cudaMemsetAsync(d_code, 0, sizeof(uint32_t) * std::max<uint64_t>(P_total, 1), st)));
     if (nC)
-        k_pb_place<<<nC, PBB_THREADS, smem_place, st>>>(g->csr_off, g->csr_col, d_cs, d_abase, d_tab, sh, ntab,
+        k_pb_place<<<nC, PBP_THREADS, smem_place, st>>>(g->csr_off, g->csr_col, d_cs, d_abase, d_tab, sh, ntab,
                                                         d_bstart, d_bbase, nb, d_M, d_O, d_runs, d_src, d_dst);
     PBK(cuda_err(cudaGetLastError()));
 
