@@ -677,7 +677,7 @@ static int build_in_rows(ip_graph* g, cudaStream_t st) {
 
 int ensure_in_rows(ip_graph* g, cudaStream_t st) { return g->csc_rows_pending ? build_in_rows(g, st) : IP_OK; }
 
-static int relabel(ip_graph* g, cudaStream_t st);
+static int relabel(ip_graph* g, cudaStream_t st, const uint32_t* hcol = nullptr, const uint32_t* hw = nullptr);
 
 static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, const uint32_t* csr_col,
                   const uint32_t* csr_w, const uint32_t* csc_off, const uint32_t* csc_row, const uint32_t* csc_w,
@@ -701,10 +701,24 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
 
     const bool alias = csc_off != nullptr && csc_off == csr_off && csc_row == csr_col;
     const size_t ea = edge_alloc_count(E);
+    // Renumbered from page-locked host arrays (and no separate CSC to copy): the
+    // renumbering reads the edges from the host itself (k_rl_host_edges), so they are
+    // not first uploaded in the caller's numbering.
+    const uint32_t* hcol = nullptr;
+    const uint32_t* hw = nullptr;
+    if (renumber && !device_ptrs && E && (alias || !csc_off)) {
+        hcol = mapped_host(csr_col);
+        hw = csr_w ? mapped_host(csr_w) : nullptr;
+        if (csr_w && !hw) hcol = nullptr;
+    }
     if ((r = upload(g, &g->csr_off, csr_off, (size_t)n + 1, (size_t)n + 1, device_ptrs, st))) return r;
     bool ids_checked = false;
-    if ((r = upload(g, &g->csr_col, csr_col, E, ea, device_ptrs, st, n, &ids_checked))) return r;
-    if (csr_w && (r = upload(g, &g->csr_w, csr_w, E, ea, device_ptrs, st))) return r;
+    if (hcol) {
+        ids_checked = true;  // by k_rl_host_edges
+    } else {
+        if ((r = upload(g, &g->csr_col, csr_col, E, ea, device_ptrs, st, n, &ids_checked))) return r;
+        if (csr_w && (r = upload(g, &g->csr_w, csr_w, E, ea, device_ptrs, st))) return r;
+    }
     // validated on the device whether the caller's arrays were host or device memory
     if ((r = validate_device(g, g->csr_off, g->csr_col, st, ids_checked))) return r;
     if (alias) {
@@ -721,7 +735,7 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
     } else if (!renumber && (r = build_in_offsets(g, st))) {
         return r;
     }
-    if (csr_w && csc_off && !g->csc_w) return IP_E_INVAL;
+    if (csr_w && csc_off && !alias && !g->csc_w) return IP_E_INVAL;
 
     // per-vertex arrays
     const size_t nv = (size_t)n;
@@ -757,7 +771,7 @@ static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, 
     CK(cudaEventCreate(&g->ev0));
     CK(cudaEventCreate(&g->ev1));
     if (renumber) {
-        if ((r = relabel(g, st))) return r;  // transposes (directed) and builds the bins
+        if ((r = relabel(g, st, hcol, hw))) return r;  // transposes (directed) and builds the bins
     } else {
         if ((r = ensure_bins(g, DEFAULT_T1, DEFAULT_T2, st))) return r;
     }
@@ -872,6 +886,67 @@ __global__ void k_rl_edges(const uint32_t* __restrict__ off_new, const uint32_t*
     }
 }
 
+// The renumbered CSR read straight from the caller's page-locked host arrays (mapped
+// into the device's address space), for creation with renumbering: the edges cross
+// the host link once and are never stored in the caller's numbering. Warps take
+// chunks of RL_CH old edge positions and read them in order (coalesced), check every
+// id (< n; otherwise bit 2 of *err, as k_validate_ids, and the edge is written as 0)
+// and write each edge at its new position with its new id. A warp keeps the first old
+// and new positions of 32 consecutive old sources in registers and finds each lane's
+// source by a 5-step shuffle search.
+__global__ void __launch_bounds__(256) k_rl_host_edges(const uint32_t* __restrict__ off_old,
+                                                       const uint32_t* __restrict__ off_new,
+                                                       const uint32_t* __restrict__ new_of_old,
+                                                       const uint32_t* __restrict__ chunk_src,
+                                                       const uint32_t* __restrict__ hcol,
+                                                       const uint32_t* __restrict__ hw, uint32_t n, uint64_t E,
+                                                       uint32_t n_chunks, uint32_t* __restrict__ col_new,
+                                                       uint32_t* __restrict__ w_new, unsigned int* err) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    bool bad = false;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += nw) {
+        const uint64_t p0 = (uint64_t)c * RL_CH;
+        const uint64_t p1 = p0 + RL_CH < E ? p0 + RL_CH : E;
+        for (uint64_t s = chunk_src[c];; s += 32) {  // windows of 32 old sources
+            const uint64_t sl = s + lane;
+            const uint32_t wo = sl < n ? off_old[sl] : (uint32_t)E;          // the lane's source: first old position
+            const uint32_t wn = sl < n ? off_new[new_of_old[sl]] : 0u;       // and first new position
+            const uint64_t wend = s + 32 <= n ? (uint64_t)off_old[s + 32] : E;
+            const uint64_t w0 = __shfl_sync(FULL, wo, 0);
+            const uint64_t lo = p0 > w0 ? p0 : w0, hi = p1 < wend ? p1 : wend;
+            for (uint64_t base = lo; base < hi; base += 32 * RL_UNROLL) {
+                uint32_t q[RL_UNROLL], pos[RL_UNROLL], cv[RL_UNROLL], wv[RL_UNROLL];
+#pragma unroll
+                for (uint32_t u = 0; u < RL_UNROLL; ++u) {
+                    const uint64_t qq = base + 32 * u + lane;
+                    q[u] = qq < hi ? (uint32_t)qq : 0xFFFFFFFFu;
+                    uint32_t i = 0;  // largest i with wo(i) <= q
+#pragma unroll
+                    for (uint32_t step = 16; step; step >>= 1)
+                        if (__shfl_sync(FULL, wo, i + step) <= q[u]) i += step;
+                    pos[u] = __shfl_sync(FULL, wn, i) + (q[u] - __shfl_sync(FULL, wo, i));
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < RL_UNROLL; ++u) {
+                    cv[u] = q[u] != 0xFFFFFFFFu ? hcol[q[u]] : 0u;
+                    wv[u] = (hw && q[u] != 0xFFFFFFFFu) ? hw[q[u]] : 0u;
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < RL_UNROLL; ++u)
+                    if (q[u] != 0xFFFFFFFFu) {
+                        const bool ok = cv[u] < n;
+                        bad |= !ok;
+                        col_new[pos[u]] = ok ? new_of_old[cv[u]] : 0u;
+                        if (hw) w_new[pos[u]] = wv[u];
+                    }
+            }
+            if (wend >= p1) break;
+        }
+    }
+    if (bad) atomicOr(err, 2u);
+}
+
 // out[old] = in[new_of_old[old]] (a per-vertex array back to the caller's numbering).
 __global__ void k_rl_unpermute(const uint32_t* __restrict__ in, const uint32_t* __restrict__ new_of_old, uint32_t n,
                                uint32_t* out) {
@@ -884,7 +959,9 @@ int unpermute(const ip_graph* g, const uint32_t* in, uint32_t* out, cudaStream_t
     return cuda_err(cudaGetLastError());
 }
 
-static int relabel(ip_graph* g, cudaStream_t st) {
+// hcol / hw: the caller's page-locked CSR columns and weights (device-visible
+// addresses) when creation reads them here instead of uploading them first.
+static int relabel(ip_graph* g, cudaStream_t st, const uint32_t* hcol, const uint32_t* hw) {
     if (g->new_of_old) return IP_OK;
     const uint32_t n = g->V;
     const uint64_t E = g->E;
@@ -905,7 +982,7 @@ static int relabel(ip_graph* g, cudaStream_t st) {
     if ((r = alloc_dev(g, (void**)&chunk_src, (size_t)n_chunks * 4))) return r;
     if ((r = alloc_dev(g, (void**)&col_new, ea * 4))) return r;
     CK(cudaMemsetAsync(col_new + E, 0, (ea - E) * 4, st));  // the padding after the last edge
-    if (g->csr_w) {
+    if (g->csr_w || hw) {
         if ((r = alloc_dev(g, (void**)&w_new, ea * 4))) return r;
         CK(cudaMemsetAsync(w_new + E, 0, (ea - E) * 4, st));
     }
@@ -926,7 +1003,13 @@ static int relabel(ip_graph* g, cudaStream_t st) {
     k_rl_place<<<nblk, 32, 0, st>>>(g->csr_off, n, R, pos, g->new_of_old, g->old_of_new, off_new, start_old);
     CK(cudaGetLastError());
     if ((r = exclusive_scan(g, off_new, (uint64_t)n + 1, st))) return r;  // out-degrees -> offsets
-    if (E) {
+    if (E && hcol) {  // chunks of old positions, read from the host arrays
+        k_rl_chunk_src<<<grid_for(g, n_chunks), 256, 0, st>>>(g->csr_off, n, n_chunks, chunk_src);
+        CK(cudaGetLastError());
+        k_rl_host_edges<<<g->num_sms * 8, 256, 0, st>>>(g->csr_off, off_new, g->new_of_old, chunk_src, hcol, hw, n, E,
+                                                       n_chunks, col_new, w_new, &g->ctl->err);
+        CK(cudaGetLastError());
+    } else if (E) {
         k_rl_chunk_src<<<grid_for(g, n_chunks), 256, 0, st>>>(off_new, n, n_chunks, chunk_src);
         CK(cudaGetLastError());
         k_rl_edges<<<grid_for(g, (uint64_t)n_chunks * 32), 256, 0, st>>>(
@@ -936,6 +1019,17 @@ static int relabel(ip_graph* g, cudaStream_t st) {
     // Every buffer of the old numbering goes back to the device cache (the rebuilt
     // degree bins have the same sizes and take theirs back): the device is idle first.
     CK(cudaDeviceSynchronize());
+    if (hcol) {  // the ids read from the host were checked on the way
+        unsigned int h = 0;
+        CK(cudaMemcpy(&h, &g->ctl->err, sizeof(h), cudaMemcpyDeviceToHost));
+        if (h & 2u) {
+            DeviceIdleScope idle;
+            for (uint32_t* p : {hist, pos, off_new, start_old, chunk_src, col_new, w_new}) free_dev(p);
+            g->device_bytes -= (size_t)nblk * RL_KEYS * 8 + ((size_t)n + 1) * 4 + (size_t)n * 4 +
+                               (size_t)n_chunks * 4 + ea * 4 * (w_new ? 2 : 1);
+            return IP_E_RANGE;
+        }
+    }
     const bool alias = g->csc_alias;
     {
         DeviceIdleScope idle;
@@ -956,7 +1050,7 @@ static int relabel(ip_graph* g, cudaStream_t st) {
         free_dev(g->csr_off);
         free_dev(g->csr_col);
         free_dev(g->csr_w);
-        g->device_bytes -= ((size_t)n + 1) * 4 + ea * 4 * (g->csr_w ? 2 : 1);
+        g->device_bytes -= ((size_t)n + 1) * 4 + (g->csr_col ? ea * 4 : 0) + (g->csr_w ? ea * 4 : 0);
         free_graph_exec(g);
         free_batch_state(g);
         pb_free(g);

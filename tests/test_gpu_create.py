@@ -1,6 +1,7 @@
 """Graph creation from page-locked host arrays: such arrays are read by the
-device directly (a copy kernel that also checks the vertex ids), every other
-host array by a DMA copy. Both routes must build the same graph: results against
+device directly (a copy kernel that also checks the vertex ids, or, when the
+graph is renumbered during creation, the renumbering copy itself, which checks
+them too), every other host array by a DMA copy. Both routes must build the same graph: results against
 the oracle for CSR-only, CSR + CSC and symmetric inputs with edge counts that are
 not multiples of 4, a misaligned page-locked view (DMA route), and an
 out-of-range id or a decreasing offset refused with the same codes as the check
@@ -29,14 +30,15 @@ def _pin(a, offset=0):
     return t[offset:]
 
 
+@pytest.mark.parametrize("relabel", [False, True])
 @pytest.mark.parametrize("offset", [0, 1])
-def test_pinned_inputs_build_the_same_graph(offset):
+def test_pinned_inputs_build_the_same_graph(offset, relabel):
     g = inputs.rmat_graph(11, symmetrize=True, weighted=True, seed=3)
     assert g.m % 4 != 0 or offset
     ref = {"hashmin": oracle.hashmin(g.n, g.row_ptr, g.col)[0], "sssp": oracle.sssp(g.n, g.row_ptr, g.col, g.w)[0]}
     p = [_pin(x, offset) for x in (g.row_ptr, g.col, g.w)]
     assert p[1].is_pinned()
-    with ipg.Graph(g.n, p[0], p[1], p[2], symmetric=True) as G:
+    with ipg.Graph(g.n, p[0], p[1], p[2], symmetric=True, relabel=relabel) as G:
         for app in ("hashmin", "sssp"):
             G.run(app)
             assert np.array_equal(G.values(app), ref[app]), app
@@ -45,27 +47,29 @@ def test_pinned_inputs_build_the_same_graph(offset):
     for csc in (False, True):
         arrs = [_pin(d.row_ptr, offset), _pin(d.col, offset)]
         kw = dict(csc_offsets=_pin(d.t_ptr, offset), csc_rows=_pin(d.t_idx, offset)) if csc else {}
-        with ipg.Graph(d.n, *arrs, **kw) as G:
+        with ipg.Graph(d.n, *arrs, relabel=relabel, **kw) as G:
             G.run("pagerank")
             got = G.values("pagerank").astype(np.float64)
         assert float(np.max(np.abs(got - want) / want)) <= 1e-5
 
 
+@pytest.mark.parametrize("relabel", [False, True])
 @pytest.mark.parametrize("offset", [0, 1])
-def test_pinned_inputs_are_checked(offset):
+def test_pinned_inputs_are_checked(offset, relabel):
     g = inputs.rmat_graph(10, symmetrize=True, seed=5)
     col = g.col.copy()
     col[-1] = g.n + 3  # the last word: the copy kernel's tail when E is not a multiple of 4
     col[len(col) // 3] = g.n
     with pytest.raises(ipg.IPError) as e:
-        ipg.Graph(g.n, _pin(g.row_ptr, offset), _pin(col, offset), symmetric=True)
+        ipg.Graph(g.n, _pin(g.row_ptr, offset), _pin(col, offset), symmetric=True, relabel=relabel)
     assert e.value.code == ipg.IP_E_RANGE
     off = g.row_ptr.copy()
     off[5] = off[6] + 1  # decreasing
     with pytest.raises(ipg.IPError) as e:
-        ipg.Graph(g.n, _pin(off, offset), _pin(g.col, offset), symmetric=True)
+        ipg.Graph(g.n, _pin(off, offset), _pin(g.col, offset), symmetric=True, relabel=relabel)
     assert e.value.code == ipg.IP_E_INVAL
-    with ipg.Graph(g.n, _pin(g.row_ptr, offset), _pin(g.col, offset), symmetric=True) as G:  # and then a good one
+    with ipg.Graph(g.n, _pin(g.row_ptr, offset), _pin(g.col, offset), symmetric=True,
+                   relabel=relabel) as G:  # and then a good one
         G.run("hashmin")
         assert np.array_equal(G.values("hashmin"), oracle.hashmin(g.n, g.row_ptr, g.col)[0])
 
