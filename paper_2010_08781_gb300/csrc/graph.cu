@@ -893,7 +893,9 @@ __global__ void k_rl_edges(const uint32_t* __restrict__ off_new, const uint32_t*
 // id (< n; otherwise bit 2 of *err, as k_validate_ids, and the edge is written as 0)
 // and write each edge at its new position with its new id. A warp keeps the first old
 // and new positions of 32 consecutive old sources in registers and finds each lane's
-// source by a 5-step shuffle search.
+// source by a 5-step shuffle search. With cnt (a directed graph), the in-degrees of
+// the new ids are counted on the way, as k_count_in does (the first CI_HOT vertices'
+// counters in dynamic shared memory, CI_HOT words), while the link is the bound.
 __global__ void __launch_bounds__(256) k_rl_host_edges(const uint32_t* __restrict__ off_old,
                                                        const uint32_t* __restrict__ off_new,
                                                        const uint32_t* __restrict__ new_of_old,
@@ -901,7 +903,12 @@ __global__ void __launch_bounds__(256) k_rl_host_edges(const uint32_t* __restric
                                                        const uint32_t* __restrict__ hcol,
                                                        const uint32_t* __restrict__ hw, uint32_t n, uint64_t E,
                                                        uint32_t n_chunks, uint32_t* __restrict__ col_new,
-                                                       uint32_t* __restrict__ w_new, unsigned int* err) {
+                                                       uint32_t* __restrict__ w_new, uint32_t* cnt,
+                                                       unsigned int* err) {
+    extern __shared__ uint32_t hot[];
+    const uint32_t H = cnt ? min(n, CI_HOT) : 0u;
+    for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) hot[i] = 0;
+    __syncthreads();
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     bool bad = false;
@@ -937,14 +944,24 @@ __global__ void __launch_bounds__(256) k_rl_host_edges(const uint32_t* __restric
                     if (q[u] != 0xFFFFFFFFu) {
                         const bool ok = cv[u] < n;
                         bad |= !ok;
-                        col_new[pos[u]] = ok ? new_of_old[cv[u]] : 0u;
+                        const uint32_t v = ok ? new_of_old[cv[u]] : 0u;
+                        col_new[pos[u]] = v;
                         if (hw) w_new[pos[u]] = wv[u];
+                        if (cnt && ok) {
+                            if (v < H)
+                                atomicAdd(hot + v, 1u);
+                            else
+                                atomicAdd(cnt + v, 1u);
+                        }
                     }
             }
             if (wend >= p1) break;
         }
     }
     if (bad) atomicOr(err, 2u);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < H; i += blockDim.x)
+        if (hot[i]) atomicAdd(cnt + i, hot[i]);
 }
 
 // out[old] = in[new_of_old[old]] (a per-vertex array back to the caller's numbering).
@@ -1003,11 +1020,17 @@ static int relabel(ip_graph* g, cudaStream_t st, const uint32_t* hcol, const uin
     k_rl_place<<<nblk, 32, 0, st>>>(g->csr_off, n, R, pos, g->new_of_old, g->old_of_new, off_new, start_old);
     CK(cudaGetLastError());
     if ((r = exclusive_scan(g, off_new, (uint64_t)n + 1, st))) return r;  // out-degrees -> offsets
+    uint32_t* in_cnt = nullptr;  // in-degrees counted by the host read (directed graphs)
     if (E && hcol) {  // chunks of old positions, read from the host arrays
+        if (!g->csc_alias) {
+            if ((r = alloc_dev(g, (void**)&in_cnt, ((size_t)n + 1) * 4))) return r;
+            CK(cudaMemsetAsync(in_cnt, 0, ((size_t)n + 1) * 4, st));
+        }
         k_rl_chunk_src<<<grid_for(g, n_chunks), 256, 0, st>>>(g->csr_off, n, n_chunks, chunk_src);
         CK(cudaGetLastError());
-        k_rl_host_edges<<<g->num_sms * 8, 256, 0, st>>>(g->csr_off, off_new, g->new_of_old, chunk_src, hcol, hw, n, E,
-                                                       n_chunks, col_new, w_new, &g->ctl->err);
+        k_rl_host_edges<<<g->num_sms * 6, 256, in_cnt ? CI_HOT * 4 : 0, st>>>(
+            g->csr_off, off_new, g->new_of_old, chunk_src, hcol, hw, n, E, n_chunks, col_new, w_new, in_cnt,
+            &g->ctl->err);
         CK(cudaGetLastError());
     } else if (E) {
         k_rl_chunk_src<<<grid_for(g, n_chunks), 256, 0, st>>>(off_new, n, n_chunks, chunk_src);
@@ -1024,9 +1047,9 @@ static int relabel(ip_graph* g, cudaStream_t st, const uint32_t* hcol, const uin
         CK(cudaMemcpy(&h, &g->ctl->err, sizeof(h), cudaMemcpyDeviceToHost));
         if (h & 2u) {
             DeviceIdleScope idle;
-            for (uint32_t* p : {hist, pos, off_new, start_old, chunk_src, col_new, w_new}) free_dev(p);
+            for (uint32_t* p : {hist, pos, off_new, start_old, chunk_src, col_new, w_new, in_cnt}) free_dev(p);
             g->device_bytes -= (size_t)nblk * RL_KEYS * 8 + ((size_t)n + 1) * 4 + (size_t)n * 4 +
-                               (size_t)n_chunks * 4 + ea * 4 * (w_new ? 2 : 1);
+                               (size_t)n_chunks * 4 + ea * 4 * (w_new ? 2 : 1) + (in_cnt ? ((size_t)n + 1) * 4 : 0);
             return IP_E_RANGE;
         }
     }
@@ -1069,6 +1092,10 @@ static int relabel(ip_graph* g, cudaStream_t st, const uint32_t* hcol, const uin
         g->csc_off = g->csr_off;
         g->csc_row = g->csr_col;
         g->csc_w = g->csr_w;
+    } else if (in_cnt) {  // counted during the host read: the offsets are their scan
+        g->csc_off = in_cnt;
+        if ((r = exclusive_scan(g, g->csc_off, (uint64_t)n + 1, st))) return r;
+        g->csc_rows_pending = true;
     } else if ((r = build_in_offsets(g, st))) {
         return r;
     }
