@@ -687,6 +687,7 @@ __global__ void k_pb_colscan(const uint32_t* __restrict__ M, uint32_t* O, uint32
 }
 
 constexpr uint32_t PB_PIECE = 1024;  // out-edges per warp task of k_pb_place
+constexpr int PB_PU = 4;             // k_pb_place: out-edges per lane in flight
 
 // Per chunk: the run records (padded to 4 entries, the padding reads source `ns`
 // whose code is the neutral one), then every out-edge into its run in both orders.
@@ -775,33 +776,39 @@ __global__ void __launch_bounds__(PBP_THREADS, 1) k_pb_place(const uint32_t* __r
             else
                 hi = mid - 1;
         }
-        uint32_t ws = lo;                              // first source of the window
-        uint32_t a = offs[min(ws + lane, ns)];         // lane i: first edge of source ws + i
-        uint32_t wend = offs[min(ws + 32, ns)];        // first edge after the window
-        for (uint32_t base = p0; base < p1; base += 32) {
-            const uint32_t e = base + lane;
-            bool pending = e < p1;
-            while (__any_sync(FULL, pending)) {  // warp-uniform: every lane takes part in the shuffles
-                uint32_t j = 0;                     // the last lane j with a_j <= e
+        for (uint32_t ws = lo;; ws += 32) {                   // windows of 32 sources
+            const uint32_t a = offs[min(ws + lane, ns)];      // lane i: first edge of source ws + i
+            const uint32_t wend = offs[min(ws + 32, ns)];     // first edge after the window
+            const uint32_t whi = min(p1, wend);
+            const uint32_t wlo = max(p0, __shfl_sync(FULL, a, 0));
+            for (uint32_t base = wlo; base < whi; base += 32 * PB_PU) {  // PB_PU edges per lane in flight
+                uint32_t e[PB_PU], jv[PB_PU], v[PB_PU], q[PB_PU], b[PB_PU];
 #pragma unroll
-                for (uint32_t k = 16; k; k >>= 1) {
-                    const uint32_t aj = __shfl_sync(FULL, a, j + k);
-                    if (aj <= e) j += k;
+                for (int u = 0; u < PB_PU; ++u) {
+                    e[u] = base + 32 * u + lane;
+                    uint32_t jj = 0;  // the last lane jj with a_jj <= e
+#pragma unroll
+                    for (uint32_t k = 16; k; k >>= 1) {
+                        const uint32_t aj = __shfl_sync(FULL, a, jj + k);
+                        if (aj <= e[u]) jj += k;
+                    }
+                    jv[u] = jj;
                 }
-                if (pending && e < wend) {
-                    const uint32_t v = col[e];
-                    const uint32_t q = pb_bin_of(v, tab, sh, bstart);
-                    const uint32_t k = atomicAdd(cur + q, 1u);
-                    src[a_c + cnt[q] + k] = (uint16_t)(ws + j);
-                    dst[rb[q] + k] = (uint16_t)(v - __ldg(bstart + q));
-                    pending = false;
-                }
-                if (__any_sync(FULL, pending)) {  // some lane's edge lies past the window: slide it
-                    ws = min(ws + 32, ns - 1);
-                    a = offs[min(ws + lane, ns)];
-                    wend = offs[min(ws + 32, ns)];
-                }
+#pragma unroll
+                for (int u = 0; u < PB_PU; ++u) v[u] = e[u] < whi ? col[e[u]] : 0u;
+#pragma unroll
+                for (int u = 0; u < PB_PU; ++u) q[u] = e[u] < whi ? pb_bin_of(v[u], tab, sh, bstart) : 0u;
+#pragma unroll
+                for (int u = 0; u < PB_PU; ++u) b[u] = e[u] < whi ? __ldg(bstart + q[u]) : 0u;
+#pragma unroll
+                for (int u = 0; u < PB_PU; ++u)
+                    if (e[u] < whi) {
+                        const uint32_t k = atomicAdd(cur + q[u], 1u);
+                        src[a_c + cnt[q[u]] + k] = (uint16_t)(ws + jv[u]);
+                        dst[rb[q[u]] + k] = (uint16_t)(v[u] - b[u]);
+                    }
             }
+            if (wend >= p1) break;
         }
     }
 }
