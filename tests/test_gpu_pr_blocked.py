@@ -138,6 +138,22 @@ def test_rmat20_and_determinism():
     assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
+def test_rmat22_thirty_updates_against_the_oracle():
+    """The whole T = 30 trajectory at R-MAT 22 (65M edges: the engine AUTO picks from
+    2^24 edges, renumbered, over a thousand chunks and bins) against the FP64
+    oracle's 30 updates, every vertex: the fixed-point sums keep the per-vertex
+    error within the bar after 30 rounds of feeding the engine's own ranks back."""
+    g = inputs.rmat_graph(22, seed=1)
+    want, _ = _ref(g)
+    with ipg.Graph.from_inputs(g) as G:
+        st = G.run("pagerank")  # AUTO engine, default policy: the configuration the bench times
+        got = G.values("pagerank")
+        assert st.supersteps == 31
+        assert G.info()["bytes_blocked_layout"] > 0  # the blocked engine ran
+    assert _err(got, want) <= PR_RTOL
+    assert abs(float(np.sum(got.astype(np.float64))) - float(np.sum(want))) <= 1e-4
+
+
 def test_mode_sequences_and_auto_policy():
     g = inputs.rmat_graph(14, seed=3)
     want, _ = _ref(g)
