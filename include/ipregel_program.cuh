@@ -22,6 +22,16 @@
  *                                                         // returns the value unchanged and never the
  *                                                         // all-ones pattern: the pull may stream the
  *                                                         // blocked edge layout (Hashmin)
+ *     // optional (false when absent):
+ *     static constexpr bool kBlockedMinPullAddsWeight = ...;  // Combiner is MinCombiner<uint32_t>,
+ *                                                         // message(value, w) is value + w and every value
+ *                                                         // the program broadcasts is at most (V - 1) times
+ *                                                         // the largest weight: the pull may stream the
+ *                                                         // blocked layout with the weights stored there as
+ *                                                         // one byte per edge, on graphs whose weights are
+ *                                                         // below 256 and V times the largest weight below
+ *                                                         // 2^32 - 1, so that no message reaches the
+ *                                                         // all-ones pattern (SSSP)
  *     // superstep 0 (the first superstep, Section 4.3.1 condition 1): set the initial
  *     // value and return whether the vertex broadcasts it (caller_id: the vertex's id
  *     // in the caller's numbering; source: ip_options_t.source in the internal one)
@@ -152,6 +162,13 @@ template <class C, class = void>
 struct has_improves : std::false_type {};
 template <class C>
 struct has_improves<C, std::void_t<decltype(C::improves(typename C::T(), typename C::T()))>> : std::true_type {};
+
+// A program's optional kBlockedMinPullAddsWeight (false when it declares none).
+template <class P, class = void>
+struct blocked_pull_adds_weight : std::false_type {};
+template <class P>
+struct blocked_pull_adds_weight<P, std::void_t<decltype(P::kBlockedMinPullAddsWeight)>>
+    : std::integral_constant<bool, P::kBlockedMinPullAddsWeight> {};
 
 // Does this combiner map to one hardware atomic on sm_103a?
 template <class C>

@@ -39,7 +39,9 @@ struct SsspProgram {
     static constexpr bool kAllBroadcastAtStart = false;
     static constexpr bool kUsesSource = true;
     static constexpr bool kEarlyExitUnweighted = true;
-    static constexpr bool kBlockedMinPull = false;  // the message reads the edge weight
+    static constexpr bool kBlockedMinPull = false;  // the message reads the edge weight,
+    static constexpr bool kBlockedMinPullAddsWeight = true;  // and adds it: a broadcast distance is a
+                                                             // path's length, at most (V - 1) x max weight
     __device__ static bool init(uint32_t v, uint32_t, uint32_t source, Value& value) {
         value = v == source ? 0u : 0xFFFFFFFFu;
         return v == source;

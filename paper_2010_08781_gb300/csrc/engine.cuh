@@ -34,7 +34,8 @@ struct ProgramOps {
     const char* name;
     bool uses_source;       // reads ip_options_t.source (range-checked, mapped when renumbered)
     bool float_values;      // values are FP32 (ip_get_values returns floats)
-    bool blocked_min_pull;  // the pull may run on the blocked layout (pb.cu)
+    int blocked_kind;       // the pull may run on the blocked layout (pb.cu): 0 no, PB_MIN_COPY (the
+                            // codes are the broadcasts), PB_MIN_ADD_WEIGHT (broadcast + edge weight)
     int (*prepare)(const ip_graph* g);  // occupancy queries, before any stream capture
     int (*init)(const ip_graph* g, const Params& P, cudaStream_t st);
     // exchange + apply of one superstep in `mode`; with ev (4 events), the boundaries
@@ -514,8 +515,12 @@ int cuda_err(cudaError_t e);
 // Launch sizes and the host entry points of one program's kernels.
 template <class PROG>
 struct ProgramEngine {
-    static_assert(!PROG::kBlockedMinPull || std::is_same<typename PROG::Combiner, ipregel::MinCombiner<uint32_t>>::value,
+    static constexpr bool kAddsWeight = ipregel::blocked_pull_adds_weight<PROG>::value;
+    static_assert(!(PROG::kBlockedMinPull || kAddsWeight) ||
+                      std::is_same<typename PROG::Combiner, ipregel::MinCombiner<uint32_t>>::value,
                   "the blocked pull folds uint32 broadcast slots with min");
+    static_assert(!(PROG::kBlockedMinPull && kAddsWeight), "one kind of blocked pull per program");
+    static constexpr int kBlockedKind = PROG::kBlockedMinPull ? PB_MIN_COPY : (kAddsWeight ? PB_MIN_ADD_WEIGHT : 0);
     enum { K_PUSH_S, K_PUSH_D, K_PULL, K_PULL_EARLY, K_MISC, K_COUNT };
     static int occ[K_COUNT];  // resident CTAs per SM of each kernel, queried once
     static std::once_flag once;
@@ -565,8 +570,8 @@ struct ProgramEngine {
                 break;
             default:
                 mark(1);
-                if (PROG::kBlockedMinPull && P.pb.on) {
-                    const int r = pb_min_launch(g, P, st);
+                if (kBlockedKind && P.pb.on) {
+                    const int r = pb_min_launch(g, P, st, kBlockedKind);
                     if (r != IP_OK) return r;
                 } else if (PROG::kEarlyExitUnweighted && P.pull_early_exit)
                     eng::k_pull<PROG, true><<<n * occ[K_PULL_EARLY], BLOCK, 0, st>>>(P);
@@ -585,7 +590,7 @@ struct ProgramEngine {
         o.name = name;
         o.uses_source = PROG::kUsesSource;
         o.float_values = std::is_floating_point<typename PROG::Value>::value;
-        o.blocked_min_pull = PROG::kBlockedMinPull;
+        o.blocked_kind = kBlockedKind;
         o.prepare = &prepare;
         o.init = &init;
         o.superstep = &superstep;

@@ -677,6 +677,35 @@ static int build_in_rows(ip_graph* g, cudaStream_t st) {
 
 int ensure_in_rows(ip_graph* g, cudaStream_t st) { return g->csc_rows_pending ? build_in_rows(g, st) : IP_OK; }
 
+__global__ void k_max_words(const uint32_t* __restrict__ a, uint64_t n, unsigned int* out) {
+    uint32_t m = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        m = max(m, a[i]);
+    m = __reduce_max_sync(FULL, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+int graph_max_weight(ip_graph* g, cudaStream_t st) {
+    if (!g->weighted || g->max_w_known) return IP_OK;
+    unsigned int* mx = nullptr;
+    int r = alloc_dev(g, (void**)&mx, sizeof(unsigned int));
+    if (r) return r;
+    uint32_t h = 0;
+    r = cuda_err(cudaMemsetAsync(mx, 0, sizeof(unsigned int), st));
+    if (!r && g->E) {
+        k_max_words<<<grid_for(g, g->E), 256, 0, st>>>(g->csr_w, g->E, mx);
+        r = cuda_err(cudaGetLastError());
+    }
+    if (!r) r = cuda_err(cudaMemcpyAsync(&h, mx, sizeof(h), cudaMemcpyDeviceToHost, st));
+    if (!r) r = cuda_err(cudaStreamSynchronize(st));
+    free_dev(mx);
+    g->device_bytes -= sizeof(unsigned int);
+    if (r) return r;
+    g->max_w = h;
+    g->max_w_known = true;
+    return IP_OK;
+}
+
 static int relabel(ip_graph* g, cudaStream_t st, const uint32_t* hcol = nullptr, const uint32_t* hw = nullptr);
 
 static int create(ip_graph* g, uint32_t n, uint64_t E, const uint32_t* csr_off, const uint32_t* csr_col,

@@ -101,6 +101,8 @@ struct PbDev {
     const uint16_t* src;     // chunk-major: source minus the first source of its chunk (padding: source count)
     const uint16_t* dst;     // [entries] bin-major: destination minus the first vertex of its bin (padding 0)
     uint32_t* code;          // [entries] bin-major: the source's broadcast as a fixed-point code (padding 0)
+    const uint8_t* w8;       // chunk-major: the entry's edge weight (graphs whose weights are below 256;
+                             // null otherwise), for the pull of PB_MIN_ADD_WEIGHT programs
     unsigned long long* big; // [V] fixed-point broadcasts of 2^31 units or more (code = 2^31 | source)
     const uint4* tasks;      // per bin {first vertex, vertices, first entry, end entry}, in bin order
     uint32_t* hi;            // [V] high words of the fixed-point sums, zero between launches
@@ -224,6 +226,8 @@ struct ip_graph {
     bool csc_alias = false;
     bool csc_rows_pending = false;  // csc_off built, csc_row / csc_w not yet (directed graphs)
     bool weighted = false;
+    bool max_w_known = false;  // max_w holds the largest edge weight (graph_max_weight)
+    uint32_t max_w = 0;
     uint32_t max_out_deg = 0, max_in_deg = 0;
     float* inv_outdeg = nullptr;
     std::vector<ipg::BinSet*> binsets;  // degree bins cached by (t1, t2), at most 4
@@ -280,7 +284,12 @@ void free_batch_state(ip_graph* g);
 // pb.cu
 int pb_prepare(ip_graph* g, cudaStream_t st, PbDev* out);
 int pb_launch(const ip_graph* g, const Params& P, cudaStream_t st);
-int pb_min_launch(const ip_graph* g, const Params& P, cudaStream_t st);  // blocked pull of a min program
+// Blocked pull of a min program: kind PB_MIN_COPY (the codes are the broadcast slots) or
+// PB_MIN_ADD_WEIGHT (broadcast + the entry's weight, 1 on unweighted graphs).
+enum { PB_MIN_COPY = 1, PB_MIN_ADD_WEIGHT = 2 };
+int pb_min_launch(const ip_graph* g, const Params& P, cudaStream_t st, int kind);
+// Largest edge weight of a weighted graph, computed once (g->max_w).
+int graph_max_weight(ip_graph* g, cudaStream_t st);
 int pb_set_mode(ip_graph* g, int min_mode, cudaStream_t st);  // neutral tail codes: 0 PageRank, 1 min programs
 bool pb_supported(const ip_graph* g);
 void pb_free(ip_graph* g);

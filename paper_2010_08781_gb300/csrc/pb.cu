@@ -93,6 +93,14 @@ __device__ __forceinline__ void pb_fixed(float v, int S, uint32_t& xl, uint32_t&
 // lane k of a step reads the 4 entries a0 + 4k.. and finds their run (for the
 // bin-major place) by a search over the window. Windows are claimed one by one
 // through *next_win (shared, 0 at the start): their sizes vary.
+// KIND: PB_COPY_CODES writes the staged codes; PB_ADD_W8 / PB_ADD_ONE (min programs
+// whose message adds the edge weight) write broadcast + the entry's weight (w8, one
+// byte per entry, chunk-major) / + 1, and the no-broadcast pattern for silent sources.
+enum { PB_COPY_CODES = 0, PB_ADD_W8 = 1, PB_ADD_ONE = 2 };
+__device__ __forceinline__ uint32_t pb_add_w(uint32_t x, uint32_t w) {
+    return x == ipregel::kNoBroadcastBits ? x : x + w;  // below the pattern: V x max weight < 2^32 - 1
+}
+template <int KIND>
 __device__ __forceinline__ void pb_copy_runs(const PbDev& B, const uint4& ch, const uint32_t* scode, uint32_t lane,
                                              uint32_t* next_win) {
     const uint32_t nwin = (ch.w - ch.z + 31) / 32;
@@ -114,7 +122,7 @@ __device__ __forceinline__ void pb_copy_runs(const PbDev& B, const uint4& ch, co
         const uint32_t delta = run.y - run.x;  // bin-major minus chunk-major place (mod 2^32)
         for (uint32_t k0 = 0; k0 < total; k0 += 32u * PB1_LOADS) {
             uint2 sv[PB1_LOADS];
-            uint32_t out[PB1_LOADS];
+            uint32_t out[PB1_LOADS], wq[PB1_LOADS];
 #pragma unroll
             for (int u = 0; u < PB1_LOADS; ++u) {
                 const uint32_t k = k0 + 32u * u + lane;
@@ -126,13 +134,22 @@ __device__ __forceinline__ void pb_copy_runs(const PbDev& B, const uint4& ch, co
                 }
                 out[u] = __shfl_sync(FULL, delta, j) + a0 + 4 * k;
                 sv[u] = k < total ? __ldcs(reinterpret_cast<const uint2*>(B.src + a0 + 4 * k)) : make_uint2(0, 0);
+                if (KIND == PB_ADD_W8)  // the 4 entries' weights: one aligned word (groups of 4 start at 4i)
+                    wq[u] = k < total ? __ldcs(reinterpret_cast<const unsigned int*>(B.w8 + a0 + 4 * k)) : 0u;
             }
 #pragma unroll
             for (int u = 0; u < PB1_LOADS; ++u)
-                if (k0 + 32u * u + lane < total)
-                    *reinterpret_cast<uint4*>(B.code + out[u]) =
-                        make_uint4(scode[sv[u].x & 0xFFFF], scode[sv[u].x >> 16], scode[sv[u].y & 0xFFFF],
-                                   scode[sv[u].y >> 16]);
+                if (k0 + 32u * u + lane < total) {
+                    uint4 c = make_uint4(scode[sv[u].x & 0xFFFF], scode[sv[u].x >> 16], scode[sv[u].y & 0xFFFF],
+                                         scode[sv[u].y >> 16]);
+                    if (KIND == PB_ADD_W8) {
+                        c = make_uint4(pb_add_w(c.x, wq[u] & 0xFF), pb_add_w(c.y, (wq[u] >> 8) & 0xFF),
+                                       pb_add_w(c.z, (wq[u] >> 16) & 0xFF), pb_add_w(c.w, wq[u] >> 24));
+                    } else if (KIND == PB_ADD_ONE) {
+                        c = make_uint4(pb_add_w(c.x, 1u), pb_add_w(c.y, 1u), pb_add_w(c.z, 1u), pb_add_w(c.w, 1u));
+                    }
+                    *reinterpret_cast<uint4*>(B.code + out[u]) = c;
+                }
         }
     }
 }
@@ -188,7 +205,7 @@ __global__ void __launch_bounds__(PB1_THREADS) k_pb_scatter(Params P) {
             next_win = 0;
         }
         __syncthreads();
-        pb_copy_runs(B, ch, scode, lane, &next_win);
+        pb_copy_runs<PB_COPY_CODES>(B, ch, scode, lane, &next_win);
         __syncthreads();
     }
 }
@@ -460,6 +477,7 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
 // per destination. A destination whose minimum is a message is a recipient (no
 // message of such a program equals the pattern): its mailbox gets the minimum and
 // its recipient bit is set, and the apply kernel runs compute() as after any pull.
+template <int KIND>
 __global__ void __launch_bounds__(PB1_THREADS) k_pbm_scatter(Params P) {
     extern __shared__ uint32_t scode[];
     __shared__ uint32_t task, next_win;
@@ -491,7 +509,7 @@ __global__ void __launch_bounds__(PB1_THREADS) k_pbm_scatter(Params P) {
             next_win = 0;
         }
         __syncthreads();
-        pb_copy_runs(B, ch, scode, lane, &next_win);
+        pb_copy_runs<KIND>(B, ch, scode, lane, &next_win);
         __syncthreads();
     }
 }
@@ -704,7 +722,8 @@ __global__ void __launch_bounds__(PBP_THREADS, 1) k_pb_place(const uint32_t* __r
                                                           const uint32_t* __restrict__ bbase, uint32_t nb,
                                                           const uint32_t* __restrict__ M,
                                                           const uint32_t* __restrict__ O, uint4* runs,
-                                                          uint16_t* src, uint16_t* dst) {
+                                                          uint16_t* src, uint16_t* dst,
+                                                          const uint32_t* __restrict__ wsrc, uint8_t* w8) {
     extern __shared__ uint32_t sm[];
     uint32_t* cnt = sm;            // [nb]: entries per bin, then the run's offset inside the chunk
     uint32_t* cur = sm + nb;       // [nb]: placement cursor
@@ -756,6 +775,7 @@ __global__ void __launch_bounds__(PBP_THREADS, 1) k_pb_place(const uint32_t* __r
             for (uint32_t k = n; k < n4; ++k) {
                 src[a_c + off + k] = (uint16_t)ns;
                 dst[rb[q] + k] = 0;
+                if (w8) w8[a_c + off + k] = 0;
             }
         }
         cnt[q] = off;
@@ -806,6 +826,7 @@ __global__ void __launch_bounds__(PBP_THREADS, 1) k_pb_place(const uint32_t* __r
                         const uint32_t k = atomicAdd(cur + q[u], 1u);
                         src[a_c + cnt[q[u]] + k] = (uint16_t)(ws + jv[u]);
                         dst[rb[q[u]] + k] = (uint16_t)(v[u] - b[u]);
+                        if (w8) w8[a_c + cnt[q[u]] + k] = (uint8_t)wsrc[e[u]];
                     }
             }
             if (wend >= p1) break;
@@ -994,10 +1015,15 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     PbDev& d = L->d;
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB1_SMEM)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB2_SMEM)));
-    PBK(cuda_err(cudaFuncSetAttribute(k_pbm_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB1_SMEM)));
+    PBK(cuda_err(cudaFuncSetAttribute(k_pbm_scatter<PB_COPY_CODES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)PB1_SMEM)));
+    PBK(cuda_err(cudaFuncSetAttribute(k_pbm_scatter<PB_ADD_W8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)PB1_SMEM)));
+    PBK(cuda_err(cudaFuncSetAttribute(k_pbm_scatter<PB_ADD_ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)PB1_SMEM)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pbm_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB2_SMEM)));
     L->grid1 = occupancy_grid(g, (const void*)k_pb_scatter, PB1_THREADS, PB1_SMEM);
-    L->grid1m = occupancy_grid(g, (const void*)k_pbm_scatter, PB1_THREADS, PB1_SMEM);
+    L->grid1m = occupancy_grid(g, (const void*)k_pbm_scatter<PB_ADD_W8>, PB1_THREADS, PB1_SMEM);
     L->grid2 = g->num_sms;  // one producer/consumer CTA per SM
 
     // chunks of consecutive sources, cut greedily on the device (pb_cuts) by edge count
@@ -1094,6 +1120,12 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     unsigned long long* d_big;
     PBK(pb_alloc(g, L, &d_runs, R));
     PBK(pb_alloc(g, L, &d_src, A));
+    // the edge weights beside the sources, one byte each, where they all fit one
+    uint8_t* d_w8 = nullptr;
+    if (g->weighted) {
+        PBK(graph_max_weight(g, st));
+        if (g->max_w <= 255) PBK(pb_alloc(g, L, &d_w8, A));
+    }
     PBK(pb_alloc(g, L, &d_dst, P_total));
     PBK(pb_alloc(g, L, &d_code, P_total));
     PBK(pb_alloc(g, L, &d_big, V));
@@ -1104,7 +1136,8 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     PBK(cuda_err(cudaMemsetAsync(d_code, 0, sizeof(uint32_t) * std::max<uint64_t>(P_total, 1), st)));
     if (nC)
         k_pb_place<<<nC, PBP_THREADS, smem_place, st>>>(g->csr_off, g->csr_col, d_cs, d_abase, d_tab, sh, ntab,
-                                                        d_bstart, d_bbase, nb, d_M, d_O, d_runs, d_src, d_dst);
+                                                        d_bstart, d_bbase, nb, d_M, d_O, d_runs, d_src, d_dst,
+                                                        g->csr_w, d_w8);
     PBK(cuda_err(cudaGetLastError()));
 
     // phase-2 tasks, one per bin, in bin order; the tail of every bin (entries after its runs)
@@ -1129,6 +1162,7 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     d.chunk = d_cs;
     d.runs = d_runs;
     d.src = d_src;
+    d.w8 = d_w8;
     d.dst = d_dst;
     d.code = d_code;
     d.big = d_big;
@@ -1168,9 +1202,14 @@ int pb_launch(const ip_graph* g, const Params& P, cudaStream_t st) {
     return cuda_err(cudaGetLastError());
 }
 
-int pb_min_launch(const ip_graph* g, const Params& P, cudaStream_t st) {
+int pb_min_launch(const ip_graph* g, const Params& P, cudaStream_t st, int kind) {
     const PbLayout* L = static_cast<const PbLayout*>(g->pb);
-    k_pbm_scatter<<<L->grid1m, PB1_THREADS, PB1_SMEM, st>>>(P);
+    if (kind == PB_MIN_COPY)
+        k_pbm_scatter<PB_COPY_CODES><<<L->grid1m, PB1_THREADS, PB1_SMEM, st>>>(P);
+    else if (g->weighted)  // run_app checked that the layout holds the weights
+        k_pbm_scatter<PB_ADD_W8><<<L->grid1m, PB1_THREADS, PB1_SMEM, st>>>(P);
+    else
+        k_pbm_scatter<PB_ADD_ONE><<<L->grid1m, PB1_THREADS, PB1_SMEM, st>>>(P);
     k_pbm_accumulate<<<L->grid2, 32 * (PB2_CONSUMERS + 1), PB2_SMEM, st>>>(P);
     return cuda_err(cudaGetLastError());
 }

@@ -798,15 +798,23 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
             if (r != IP_OK && !(r == IP_E_RANGE && o.pr_engine == IP_PR_ENGINE_AUTO)) return r;
             if (P.pb.on) CKR(pb_set_mode(g, 0, st));
         }
-    } else if (ops->blocked_min_pull) {
+    } else if (ops->blocked_kind) {
         // the blocked pull of a min program: forced, or (AUTO) once the layout exists or this
-        // handle's gather pulls have cost about as much as building it (PB_MIN_BUILD_PULLS)
-        const bool blocked = o.pr_engine == IP_PR_ENGINE_BLOCKED ||
-                             (o.pr_engine == IP_PR_ENGINE_AUTO && g->E >= PB_AUTO_EDGES && pb_supported(g) &&
-                              (g->pb || g->pull_gathered >= PB_MIN_BUILD_PULLS));
+        // handle's gather pulls have cost about as much as building it (PB_MIN_BUILD_PULLS).
+        // A program that adds the edge weight needs weights below 256 (one byte per entry in
+        // the layout) and V x the largest weight below the no-broadcast pattern.
+        bool fits = true;
+        if (ops->blocked_kind == PB_MIN_ADD_WEIGHT && g->weighted) {
+            CKR(graph_max_weight(g, st));
+            fits = g->max_w <= 255 && (uint64_t)g->V * g->max_w < 0xFFFFFFFFull;
+        }
+        const bool blocked = fits && (o.pr_engine == IP_PR_ENGINE_BLOCKED ||
+                                      (o.pr_engine == IP_PR_ENGINE_AUTO && g->E >= PB_AUTO_EDGES && pb_supported(g) &&
+                                       (g->pb || g->pull_gathered >= PB_MIN_BUILD_PULLS)));
         if (blocked) {
             const int r = pb_prepare(g, st, &P.pb);
             if (r != IP_OK && !(r == IP_E_RANGE && o.pr_engine == IP_PR_ENGINE_AUTO)) return r;
+            if (P.pb.on && ops->blocked_kind == PB_MIN_ADD_WEIGHT && g->weighted && !P.pb.w8) P.pb.on = 0;
             if (P.pb.on) CKR(pb_set_mode(g, 1, st));
         }
     }
@@ -843,7 +851,7 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     const DevCtl& c = *g->ctl_host;
     const uint32_t supersteps = c.superstep + 1;
     g->last_app = app;
-    if (ops && ops->blocked_min_pull && !P.pb.on) g->pull_gathered += c.n_pull;
+    if (ops && ops->blocked_kind && !P.pb.on) g->pull_gathered += c.n_pull;
     if (c.err & 2u) return IP_E_TIMEOUT;  // a bounded wait of a kernel ran out
     if (c.err) return IP_E_DEVICE_ASSERT;
     if (stats) {
