@@ -666,12 +666,15 @@ def c2_line(args, steps):
         msgs = sum(int(a.messages.sum()) + int(b.messages.sum()) for a, b in rs)
         kern = {}
         peak, kind = measured_peaks()
+        blocked = G.info()["bytes_blocked_layout"] > 0  # AUTO pulls on the layout once it exists
         for app, last in (("hashmin", rs[-1][0]), ("sssp", rs[-1][1])):
             seq = last.mode[1:last.supersteps].tolist()
             st = G.run(app, profile_kernels=1, stream=stream, mode_sequence=seq)
             for s in range(1, st.supersteps):
                 mode = int(st.mode[s])
                 name = KERNEL_NAMES[(MODE_NAMES[mode], app)]
+                if blocked and MODE_NAMES[mode] == "pull":
+                    name = f"k_pbm_scatter+k_pbm_accumulate ({app})"
                 by = exchange_bytes(app, mode, V, E, int(st.messages[s - 1]), int(st.broadcasters[s - 1]),
                                     int(st.active[s]))
                 k = kern.setdefault(name, [0.0, 0.0, 0])

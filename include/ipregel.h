@@ -80,16 +80,21 @@ typedef enum {
 } ip_policy_t;
 
 /* How a PULL exchange runs, for PageRank and for the vertex programs that allow
- * the blocked layout (Hashmin). Both engines compute the same combined messages;
- * they differ in how the in-neighbours' broadcasts reach the destination. */
+ * the blocked layout (Hashmin; SSSP on graphs whose weights are below 256 and
+ * whose vertex count times the largest weight is below 2^32 - 1, unweighted
+ * graphs included; the others always GATHER). Both engines compute the same
+ * combined messages; they differ in how the in-neighbours' broadcasts reach the
+ * destination. */
 typedef enum {
     IP_PR_ENGINE_AUTO = 0,    /* PageRank: BLOCKED on graphs of at least 2^24 edges that it supports,
-                                 else GATHER. Hashmin: GATHER until the handle has run 6 gather pulls
-                                 (a handle that is run again and again), BLOCKED from then on (or
-                                 whenever the layout already exists) on graphs of at least 2^24 edges */
+                                 else GATHER. Hashmin and SSSP: GATHER until the handle has run 6
+                                 gather pulls of either (a handle that is run again and again),
+                                 BLOCKED from then on (or whenever the layout already exists) on
+                                 graphs of at least 2^24 edges */
     IP_PR_ENGINE_GATHER = 1,  /* every in-edge of the CSC reads its source's broadcast */
     IP_PR_ENGINE_BLOCKED = 2  /* two streaming passes over a second edge layout built on first use
-                                 (8 bytes per edge): the sources' broadcasts are written out per
+                                 (8 bytes per edge, 9 on weighted graphs whose weights are below
+                                 256): the sources' broadcasts are written out per
                                  edge, grouped by destination bin, and every bin is summed in shared
                                  memory in 64-bit fixed point; IP_E_RANGE on graphs of more than
                                  339,738,624 vertices */
@@ -120,7 +125,7 @@ typedef struct {
     int32_t profile_kernels;      /* 1: host loop with CUDA events around every kernel; fills
                                      ip_run_stats_t.kernel_ms. Values are unchanged. */
     void* stream;                 /* cudaStream_t */
-    int32_t pr_engine;            /* ip_pr_engine_t: the PULL engine of PageRank and Hashmin
+    int32_t pr_engine;            /* ip_pr_engine_t: the PULL engine of PageRank, Hashmin and SSSP
                                      (default IP_PR_ENGINE_AUTO) */
     float pr_tolerance;           /* PageRank to convergence (the paper's Section 6.1 notes that a
                                      real PageRank runs until convergence): > 0 ends the run after
