@@ -57,13 +57,19 @@ constexpr int PB1_THREADS = 512, PBB_THREADS = 512;
 // sectors are complete instead of leaving it half written and being read back.
 constexpr int PBP_THREADS = 1024;
 constexpr size_t PBP_MIN_SMEM = 120 * 1024;
-constexpr int PB1_LOADS = 4;         // phase 1: groups of 4 entries per lane in flight
+// phase 1: groups of 4 entries per lane in flight (PageRank's scatter / the min programs')
+constexpr int PB1_LOADS_PR = 6, PB1_LOADS_MIN = 4;
 constexpr int PB_BATCH = 8;          // per-vertex loops (staging, compute()): loads in flight per thread
 constexpr int PB2_CONSUMERS = 24;    // phase 2: consumer warps (plus one producer warp)
 constexpr int PB_GROUPS = 2;        // phase 2: groups of 4 entries per consumer thread and stage
 constexpr uint32_t PB_TILE = 4 * PB_GROUPS * 32 * PB2_CONSUMERS;  // entries per stage (6144)
 constexpr int PB_STAGES = 3;         // phase 2: stages of the bulk-copy ring (108 KB)
 constexpr size_t PB1_SMEM = (PB_MAXS + 1) * sizeof(uint32_t);
+// k_pb_scatter's dynamic shared memory, padded so that two CTAs share an SM: at R-MAT 26
+// two chunks in flight per SM took 68.05 ms for T = 30 against 69.78 ms with three
+// (and 76.2 ms with one); the depth of loads in flight mattered less (4-12 groups within 0.7%)
+constexpr size_t PB1_SMEM_PR = 80 * 1024;
+constexpr size_t PB1_SMEM_MIN = PB1_SMEM;  // k_pbm_scatter's
 constexpr size_t PB2_SMEM = PB_BIN_V * sizeof(uint32_t) + (size_t)PB_STAGES * PB_TILE * (4 + 2) +
                             PB_STAGES * (32 + 16);
 
@@ -100,7 +106,7 @@ enum { PB_COPY_CODES = 0, PB_ADD_W8 = 1, PB_ADD_ONE = 2 };
 __device__ __forceinline__ uint32_t pb_add_w(uint32_t x, uint32_t w) {
     return x == ipregel::kNoBroadcastBits ? x : x + w;  // below the pattern: V x max weight < 2^32 - 1
 }
-template <int KIND>
+template <int KIND, int PB1_LOADS>
 __device__ __forceinline__ void pb_copy_runs(const PbDev& B, const uint4& ch, const uint32_t* scode, uint32_t lane,
                                              uint32_t* next_win) {
     const uint32_t nwin = (ch.w - ch.z + 31) / 32;
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(PB1_THREADS) k_pb_scatter(Params P) {
             next_win = 0;
         }
         __syncthreads();
-        pb_copy_runs<PB_COPY_CODES>(B, ch, scode, lane, &next_win);
+        pb_copy_runs<PB_COPY_CODES, PB1_LOADS_PR>(B, ch, scode, lane, &next_win);
         __syncthreads();
     }
 }
@@ -509,7 +515,7 @@ __global__ void __launch_bounds__(PB1_THREADS) k_pbm_scatter(Params P) {
             next_win = 0;
         }
         __syncthreads();
-        pb_copy_runs<KIND>(B, ch, scode, lane, &next_win);
+        pb_copy_runs<KIND, PB1_LOADS_MIN>(B, ch, scode, lane, &next_win);
         __syncthreads();
     }
 }
@@ -1013,17 +1019,17 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     PbLayout* L = new PbLayout();
     memset(&L->d, 0, sizeof(L->d));
     PbDev& d = L->d;
-    PBK(cuda_err(cudaFuncSetAttribute(k_pb_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB1_SMEM)));
+    PBK(cuda_err(cudaFuncSetAttribute(k_pb_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB1_SMEM_PR)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pb_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB2_SMEM)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pbm_scatter<PB_COPY_CODES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)PB1_SMEM)));
+                                      (int)PB1_SMEM_MIN)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pbm_scatter<PB_ADD_W8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)PB1_SMEM)));
+                                      (int)PB1_SMEM_MIN)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pbm_scatter<PB_ADD_ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)PB1_SMEM)));
+                                      (int)PB1_SMEM_MIN)));
     PBK(cuda_err(cudaFuncSetAttribute(k_pbm_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB2_SMEM)));
-    L->grid1 = occupancy_grid(g, (const void*)k_pb_scatter, PB1_THREADS, PB1_SMEM);
-    L->grid1m = occupancy_grid(g, (const void*)k_pbm_scatter<PB_ADD_W8>, PB1_THREADS, PB1_SMEM);
+    L->grid1 = occupancy_grid(g, (const void*)k_pb_scatter, PB1_THREADS, PB1_SMEM_PR);
+    L->grid1m = occupancy_grid(g, (const void*)k_pbm_scatter<PB_ADD_W8>, PB1_THREADS, PB1_SMEM_MIN);
     L->grid2 = g->num_sms;  // one producer/consumer CTA per SM
 
     // chunks of consecutive sources, cut greedily on the device (pb_cuts) by edge count
@@ -1197,7 +1203,7 @@ int pb_prepare(ip_graph* g, cudaStream_t st, PbDev* out) {
 
 int pb_launch(const ip_graph* g, const Params& P, cudaStream_t st) {
     const PbLayout* L = static_cast<const PbLayout*>(g->pb);
-    k_pb_scatter<<<L->grid1, PB1_THREADS, PB1_SMEM, st>>>(P);
+    k_pb_scatter<<<L->grid1, PB1_THREADS, PB1_SMEM_PR, st>>>(P);
     k_pb_accumulate<<<L->grid2, 32 * (PB2_CONSUMERS + 1), PB2_SMEM, st>>>(P);
     return cuda_err(cudaGetLastError());
 }
@@ -1205,11 +1211,11 @@ int pb_launch(const ip_graph* g, const Params& P, cudaStream_t st) {
 int pb_min_launch(const ip_graph* g, const Params& P, cudaStream_t st, int kind) {
     const PbLayout* L = static_cast<const PbLayout*>(g->pb);
     if (kind == PB_MIN_COPY)
-        k_pbm_scatter<PB_COPY_CODES><<<L->grid1m, PB1_THREADS, PB1_SMEM, st>>>(P);
+        k_pbm_scatter<PB_COPY_CODES><<<L->grid1m, PB1_THREADS, PB1_SMEM_MIN, st>>>(P);
     else if (g->weighted)  // run_app checked that the layout holds the weights
-        k_pbm_scatter<PB_ADD_W8><<<L->grid1m, PB1_THREADS, PB1_SMEM, st>>>(P);
+        k_pbm_scatter<PB_ADD_W8><<<L->grid1m, PB1_THREADS, PB1_SMEM_MIN, st>>>(P);
     else
-        k_pbm_scatter<PB_ADD_ONE><<<L->grid1m, PB1_THREADS, PB1_SMEM, st>>>(P);
+        k_pbm_scatter<PB_ADD_ONE><<<L->grid1m, PB1_THREADS, PB1_SMEM_MIN, st>>>(P);
     k_pbm_accumulate<<<L->grid2, 32 * (PB2_CONSUMERS + 1), PB2_SMEM, st>>>(P);
     return cuda_err(cudaGetLastError());
 }
