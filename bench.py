@@ -725,10 +725,14 @@ def run_config(args):
         src = int(np.argmax(g.out_degree()))
         with ipg.Graph.from_inputs(g) as G:
             b = {}
-            for name, kw in (("pull_early_exit", dict(policy="forced", forced_mode="pull")),
-                             ("pull_full_scan", dict(policy="forced", forced_mode="pull", pull_early_exit=0)),
-                             ("threshold_early_exit", dict(policy="threshold")),
-                             ("threshold_full_scan", dict(policy="threshold", pull_early_exit=0))):
+            # the early exit belongs to the gather pull; the blocked pull streams every entry
+            for name, kw in (("pull_early_exit", dict(policy="forced", forced_mode="pull", pr_engine="gather")),
+                             ("pull_full_scan", dict(policy="forced", forced_mode="pull", pull_early_exit=0,
+                                                     pr_engine="gather")),
+                             ("threshold_early_exit", dict(policy="threshold", pr_engine="gather")),
+                             ("threshold_full_scan", dict(policy="threshold", pull_early_exit=0, pr_engine="gather")),
+                             ("pull_blocked", dict(policy="forced", forced_mode="pull", pr_engine="blocked")),
+                             ("threshold_blocked", dict(policy="threshold", pr_engine="blocked"))):
                 rs = [G.run("sssp", source=src, **kw) for _ in range(4)][1:]
                 ms = min(r.elapsed_ms for r in rs)
                 b[name] = {"ms": round(ms, 4), "gteps": round(int(rs[0].messages.sum()) / (ms * 1e-3) / 1e9, 2),

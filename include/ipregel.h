@@ -90,7 +90,7 @@ typedef enum {
                                  else GATHER. Hashmin and SSSP: GATHER until the handle has run 6
                                  gather pulls of either (a handle that is run again and again),
                                  BLOCKED from then on (or whenever the layout already exists) on
-                                 graphs of at least 2^24 edges */
+                                 graphs of at least 2^26 edges */
     IP_PR_ENGINE_GATHER = 1,  /* every in-edge of the CSC reads its source's broadcast */
     IP_PR_ENGINE_BLOCKED = 2  /* two streaming passes over a second edge layout built on first use
                                  (8 bytes per edge, 9 on weighted graphs whose weights are below

@@ -86,6 +86,9 @@ struct Bins {
 // accumulates every bin in shared memory. Device pointers of that layout.
 constexpr uint32_t PB_BIN_V = 24576;  // most destinations per bin (one 32-bit accumulator word each in shared memory)
 constexpr uint64_t PB_AUTO_EDGES = 1ull << 24;  // IP_PR_ENGINE_AUTO picks the blocked pull from this many edges
+// ... and for min programs from this many: at R-MAT 20 (31M edges) their gather pull was
+// 7-15% faster, at R-MAT 21 (64M) even, at R-MAT 22-23 (128-259M) 8-18% slower
+constexpr uint64_t PB_MIN_AUTO_EDGES = 1ull << 26;
 // A min program's AUTO pull switches to the blocked layout once the handle has run this
 // many pull exchanges with the gather kernel (two Hashmin runs on R-MAT graphs): a handle
 // that is run again and again then pays the build once (at R-MAT 26 it costs about as

@@ -809,7 +809,7 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
             fits = g->max_w <= 255 && (uint64_t)g->V * g->max_w < 0xFFFFFFFFull;
         }
         const bool blocked = fits && (o.pr_engine == IP_PR_ENGINE_BLOCKED ||
-                                      (o.pr_engine == IP_PR_ENGINE_AUTO && g->E >= PB_AUTO_EDGES && pb_supported(g) &&
+                                      (o.pr_engine == IP_PR_ENGINE_AUTO && g->E >= PB_MIN_AUTO_EDGES && pb_supported(g) &&
                                        (g->pb || g->pull_gathered >= PB_MIN_BUILD_PULLS)));
         if (blocked) {
             const int r = pb_prepare(g, st, &P.pb);

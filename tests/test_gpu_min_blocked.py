@@ -75,11 +75,11 @@ def test_layout_shared_with_pagerank():
 
 
 def test_auto_builds_the_layout_after_enough_gather_pulls():
-    """AUTO on a graph of at least 2^24 edges: the first runs pull with the gather
+    """AUTO on a graph of at least 2^26 edges: the first runs pull with the gather
     kernel; once the handle has run 6 gather pulls the next run builds the layout
     and uses it; the labels never change."""
-    g = inputs.rmat_graph(20, symmetrize=True, seed=2)
-    assert g.m >= 1 << 24
+    g = inputs.rmat_graph(22, symmetrize=True, seed=2)
+    assert g.m >= 1 << 26
     ref = oracle.hashmin(g.n, g.row_ptr, g.col)
     with ipg.Graph.from_inputs(g) as G:
         pulls, built_at = 0, None

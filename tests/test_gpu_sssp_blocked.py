@@ -114,8 +114,8 @@ def test_heavy_weights_keep_the_gather_pull():
 
 
 def test_auto_builds_the_layout_for_sssp_after_enough_gather_pulls():
-    g = inputs.rmat_graph(20, symmetrize=True, weighted=True, seed=2)
-    assert g.m >= 1 << 24
+    g = inputs.rmat_graph(22, symmetrize=True, weighted=True, seed=2)
+    assert g.m >= 1 << 26
     ref = _ref(g, 0)
     with ipg.Graph.from_inputs(g) as G:
         pulls, built_at = 0, None
