@@ -1,8 +1,10 @@
 """The billion-edge configuration at full size (R-MAT scale 26, edge factor 16,
 (a, b, c) = (.57, .19, .19), seed 1: 67,108,864 vertices, 1,060,392,804 directed
 edges), in the launch configuration the benchmark times: the graph handed over
-as host CSR, in-edges transposed on the device, vertices renumbered by degree
-class, PageRank in forced pull with the AUTO engine (the blocked pull here).
+as page-locked host CSR (the end-to-end path: the renumbering copy reads the edges
+over the host link itself, checks them, and counts the in-degrees on the way),
+vertices renumbered by degree class, PageRank in forced pull with the AUTO engine
+(the blocked pull here).
 
 PageRank: a full FP64 oracle run takes about 11 s per superstep on one core, so
 the last superstep is checked one vertex at a time instead. With the ranks of a
@@ -30,6 +32,11 @@ SCALE = 26
 PR_RTOL = 1e-5
 
 
+def _pinned(a):
+    """A page-locked int32 copy of a uint32 array."""
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).pin_memory()
+
+
 @pytest.fixture(scope="module")
 def edges():
     return inputs.rmat_edges(SCALE, 16 << SCALE, 0.57, 0.19, 0.19, 1)
@@ -39,7 +46,7 @@ def test_pagerank_last_superstep_sampled(edges):
     g = inputs.from_edges(1 << SCALE, edges[0], edges[1])
     n, d = g.n, 0.85
     kw = dict(policy="forced", forced_mode="pull")
-    with ipg.Graph(n, g.row_ptr, g.col) as G:
+    with ipg.Graph(n, _pinned(g.row_ptr), _pinned(g.col)) as G:
         assert G.relabeled
         st29 = G.run("pagerank", pr_iterations=29, **kw)
         r29 = G.values("pagerank").astype(np.float64)
@@ -64,7 +71,8 @@ def test_pagerank_last_superstep_sampled(edges):
 
 def test_hashmin_every_label(edges):
     gs = inputs.from_edges(1 << SCALE, edges[0], edges[1], symmetrize=True)
-    with ipg.Graph.from_inputs(gs) as G:
+    ptr, col = _pinned(gs.row_ptr), _pinned(gs.col)
+    with ipg.Graph(gs.n, ptr, col, symmetric=True) as G:
         st = G.run("hashmin")
         got = G.values("hashmin")
     want, ost = oracle.hashmin(gs.n, gs.row_ptr, gs.col)
