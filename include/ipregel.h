@@ -207,10 +207,10 @@ void ip_options_default(ip_options_t* opt);
  *   csc_offsets / csc_rows / csc_weights  the in-edge (transposed) arrays in the
  *                same form; NULL csc_offsets means "build the transpose on the
  *                device": its offsets at creation, its rows and weights at the
- *                first run that reads them (a pull of a vertex program, the gather
- *                PageRank engine, a batched run; a run that cannot allocate them
- *                returns IP_E_NOMEM and leaves the graph as it was; PageRank with
- *                the blocked engine never needs them); csc_offsets == csr_offsets and csc_rows == csr_cols
+ *                first run that reads them (a pull on the gather engine, a batched
+ *                run; a run that cannot allocate them returns IP_E_NOMEM and leaves
+ *                the graph as it was; runs that pull on the blocked engine never
+ *                need them); csc_offsets == csr_offsets and csc_rows == csr_cols
  *                declares a symmetric graph and shares the arrays. csc_weights
  *                is required when csc arrays and csr_weights are both given.
  *   flags        IP_CREATE_DEVICE_PTRS: all arrays are device memory (else all are

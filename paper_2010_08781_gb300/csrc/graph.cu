@@ -611,9 +611,9 @@ static int upload(ip_graph* g, uint32_t** dst, const uint32_t* src, size_t count
 // vertex's in-edges is unspecified), in two parts. Its offsets (in-degrees counted
 // and scanned) are built with the graph: the degree bins, the blocked layout's bin
 // cuts and the maximum in-degree read them. Its rows (and weights) are built by the
-// first run that reads them (ensure_in_rows): a pull of a vertex program on the
-// gather engine, the gather PageRank engine or a batched run. The blocked PageRank
-// pull streams its own layout, so a graph that only runs it never holds the rows.
+// first run that reads them (ensure_in_rows): a pull on the gather engine or a
+// batched run. The blocked pull streams its own layout, so a graph that only pulls on
+// it never holds the rows.
 static int build_in_offsets(ip_graph* g, cudaStream_t st) {
     const uint32_t n = g->V;
     const uint64_t E = g->E;

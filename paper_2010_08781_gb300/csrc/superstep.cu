@@ -820,8 +820,8 @@ int run_app(ip_graph* g, int app, uint32_t max_supersteps, const ip_options_t* o
     }
 
     // the in-edge rows (built now if creation deferred them), unless every pull of this
-    // run streams the blocked layout: PageRank with the layout reads none
-    if (!(app == APP_PR && P.pb.on)) {
+    // run streams the blocked layout (the push exchanges read the out-edges)
+    if (!P.pb.on) {
         CKR(ensure_in_rows(g, st));
         P.csc_row = g->csc_row;
         P.csc_w = g->csc_w;

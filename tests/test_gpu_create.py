@@ -77,9 +77,9 @@ def test_pinned_inputs_are_checked(offset, relabel):
 @pytest.mark.parametrize("relabel", [False, True])
 def test_in_edge_rows_wait_for_the_first_run_that_reads_them(relabel):
     """A directed graph created without a CSC holds the transpose's offsets only. The
-    blocked PageRank pull streams its own layout and leaves it so; the first run
-    that reads in-edge rows (a pull of SSSP, the gather PageRank engine, a batched
-    run) builds them, weights included, and every result matches the oracle."""
+    blocked pull (PageRank, SSSP) streams its own layout and leaves it so; the first
+    run that reads in-edge rows (a pull on the gather engine, a batched run) builds
+    them, weights included, and every result matches the oracle."""
     d = inputs.rmat_graph(12, weighted=True, seed=6)
     ea = ((d.m + 3) // 4) * 4 + 4
     pr, _ = oracle.pagerank(d.n, d.row_ptr, d.col, T=30)
@@ -92,7 +92,10 @@ def test_in_edge_rows_wait_for_the_first_run_that_reads_them(relabel):
         got = G.values("pagerank").astype(np.float64)
         assert float(np.max(np.abs(got - pr) / pr)) <= 1e-5
         assert G.info()["bytes_graph"] == csr + (d.n + 1) * 4
-        G.run("sssp", source=srcs[0], policy="forced", forced_mode="pull")
+        G.run("sssp", source=srcs[1], policy="forced", forced_mode="pull", pr_engine="blocked")
+        assert np.array_equal(G.values("sssp"), ss[1])
+        assert G.info()["bytes_graph"] == csr + (d.n + 1) * 4
+        G.run("sssp", source=srcs[0], policy="forced", forced_mode="pull", pr_engine="gather")
         assert np.array_equal(G.values("sssp"), ss[0])
         assert G.info()["bytes_graph"] == 2 * csr
         G.run("pagerank", policy="forced", forced_mode="pull", pr_engine="gather")
