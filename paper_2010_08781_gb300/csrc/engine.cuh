@@ -369,7 +369,8 @@ __global__ void __launch_bounds__(BLOCK) k_pull(Params P) {
         }
         __syncthreads();
     }
-    for (uint32_t i = global_warp(); i < B.n_med; i += num_warps()) {
+    const uint64_t hw = (uint64_t)min(B.n_hchunk, gridDim.x) * (blockDim.x / 32);  // warps on heavy chunks
+    for (uint32_t i = rotated_warp(hw); i < B.n_med; i += num_warps()) {
         const uint32_t v = B.med[i];
         T m = C::identity();
         bool any = false;
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(BLOCK) k_pull(Params P) {
         }
     }
     const uint32_t tiles = (P.V + 31) / 32;
-    for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
+    for (uint32_t t = rotated_warp(hw + B.n_med); t < tiles; t += num_warps()) {
         const uint32_t v = t * 32 + lane_id();
         T m = C::identity();
         bool any = false;

@@ -37,6 +37,15 @@ __device__ __forceinline__ bool bit_of(const uint32_t* bm, uint32_t v) {
 }
 __device__ __forceinline__ uint32_t global_warp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
 __device__ __forceinline__ uint32_t num_warps() { return (gridDim.x * blockDim.x) >> 5; }
+// The first index of this warp in a grid-stride loop over a work list that comes
+// after `skip` warps' worth of earlier lists (the heavy vertices' CTAs, the medium
+// vertices): the warps those lists keep busy take this one last, so that on small
+// graphs the lists run side by side instead of one after another. A rotation of
+// the warps, so every item is still taken exactly once.
+__device__ __forceinline__ uint32_t rotated_warp(uint64_t skip) {
+    const uint32_t nw = num_warps();
+    return (uint32_t)((global_warp() + nw - (uint32_t)(skip % nw)) % nw);
+}
 __device__ __forceinline__ const uint32_t* bc_of(const Params& P, uint32_t s) { return (s & 1) ? P.bcast1 : P.bcast0; }
 __device__ __forceinline__ uint32_t* bc_mut(const Params& P, uint32_t s) { return (s & 1) ? P.bcast1 : P.bcast0; }
 

@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(BLOCK) k_pr_pull(Params P) {
         }
         __syncthreads();
     }
-    for (uint32_t i = global_warp(); i < B.n_med; i += num_warps()) {
+    const uint64_t hw = (uint64_t)min(B.n_hchunk, gridDim.x) * (blockDim.x / 32);  // warps on heavy chunks
+    for (uint32_t i = rotated_warp(hw); i < B.n_med; i += num_warps()) {
         const uint32_t v = B.med[i];
         float a = 0.f, c = 0.f;
         pr_gather(P.csc_row, cur, P.csc_off[v], P.csc_off[v + 1], lane_id(), 32, a, c);
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(BLOCK) k_pr_pull(Params P) {
         if (lane_id() == 0) pr_finish(P, v, a + c, s, nxt, dacc);
     }
     const uint32_t tiles = (P.V + 31) / 32;
-    for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
+    for (uint32_t t = rotated_warp(hw + B.n_med); t < tiles; t += num_warps()) {
         const uint32_t v = t * 32 + lane_id();
         if (v < P.V) {
             const uint32_t b = P.csc_off[v], e = P.csc_off[v + 1];
