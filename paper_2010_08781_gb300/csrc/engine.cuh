@@ -205,10 +205,11 @@ __global__ void __launch_bounds__(BLOCK) k_push(Params P) {
             push_range<PROG, SPARSE>(P, val_of<PROG>(P.value[u]), b, e, threadIdx.x, blockDim.x,
                                      trips_of(b, e, blockDim.x));
         }
-        // medium senders: one warp each
+        // medium senders: one warp each (first the warps the heavy chunks leave idle)
         const uint32_t nm = P.ctl->q_len[par][1];
         const uint32_t* qm = P.q[par][1];
-        for (uint32_t i = global_warp(); i < nm; i += num_warps()) {
+        const uint64_t hw = (uint64_t)min(nh, gridDim.x) * (blockDim.x / 32);
+        for (uint32_t i = rotated_warp(hw); i < nm; i += num_warps()) {
             const uint32_t u = qm[i];
             const uint32_t b = P.csr_off[u], e = P.csr_off[u + 1];
             if (lane_id() == 0) P.outbox[u] = ipregel::kNoBroadcastBits;
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(BLOCK) k_push(Params P) {
         // small senders: one lane each
         const uint32_t ns = P.ctl->q_len[par][0];
         const uint32_t* qs = P.q[par][0];
-        for (uint32_t base = global_warp() * 32; base < ns; base += num_warps() * 32) {
+        for (uint32_t base = rotated_warp(hw + nm) * 32; base < ns; base += num_warps() * 32) {
             const uint32_t i = base + lane_id();
             uint32_t b = 0, e = 0, val = 0;
             if (i < ns) {
@@ -239,7 +240,8 @@ __global__ void __launch_bounds__(BLOCK) k_push(Params P) {
                 push_range<PROG, SPARSE>(P, val_of<PROG>(P.value[ch.x]), ch.y, ch.z, threadIdx.x, blockDim.x,
                                          trips_of(ch.y, ch.z, blockDim.x));
         }
-        for (uint32_t i = global_warp(); i < B.n_med; i += num_warps()) {
+        const uint64_t hw = (uint64_t)min(B.n_hchunk, gridDim.x) * (blockDim.x / 32);
+        for (uint32_t i = rotated_warp(hw); i < B.n_med; i += num_warps()) {
             const uint32_t u = B.med[i];
             if (bit_of(bc, u)) {
                 const uint32_t b = P.csr_off[u], e = P.csr_off[u + 1];
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(BLOCK) k_push(Params P) {
             }
         }
         const uint32_t tiles = (P.V + 31) / 32;
-        for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
+        for (uint32_t t = rotated_warp(hw + B.n_med); t < tiles; t += num_warps()) {
             const uint32_t word = __ldg(bc + t);
             if (!word) continue;
             const uint32_t u = t * 32 + lane_id();

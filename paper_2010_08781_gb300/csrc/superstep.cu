@@ -207,12 +207,13 @@ __global__ void __launch_bounds__(BLOCK) k_pr_push(Params P) {
         const uint4 ch = B.hchunk[k];
         pr_scatter(P, cur[ch.x], ch.y, ch.z, threadIdx.x, blockDim.x);
     }
-    for (uint32_t i = global_warp(); i < B.n_med; i += num_warps()) {
+    const uint64_t hw = (uint64_t)min(B.n_hchunk, gridDim.x) * (blockDim.x / 32);  // warps on heavy chunks
+    for (uint32_t i = rotated_warp(hw); i < B.n_med; i += num_warps()) {
         const uint32_t u = B.med[i];
         pr_scatter(P, cur[u], P.csr_off[u], P.csr_off[u + 1], lane_id(), 32);
     }
     const uint32_t tiles = (P.V + 31) / 32;
-    for (uint32_t t = global_warp(); t < tiles; t += num_warps()) {
+    for (uint32_t t = rotated_warp(hw + B.n_med); t < tiles; t += num_warps()) {
         const uint32_t u = t * 32 + lane_id();
         if (u < P.V) {
             const uint32_t b = P.csr_off[u], e = P.csr_off[u + 1];
