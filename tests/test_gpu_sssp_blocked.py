@@ -126,3 +126,18 @@ def test_auto_builds_the_layout_for_sssp_after_enough_gather_pulls():
                 assert pulls >= 6
             pulls += st.supersteps - 1
         assert built_at is not None
+
+
+def test_vertex_count_times_weight_bound_keeps_the_gather():
+    """V x the largest weight at or above 2^32 - 1: a distance plus a weight could reach
+    the no-broadcast pattern, so SSSP keeps the gather pull (no layout is built for it)
+    and stays exact. 2^24 + 70,000 vertices, most of them isolated, weights up to 255."""
+    n = (1 << 24) + 70000
+    core = inputs.rmat_graph(14, symmetrize=True, weighted=True, seed=12)
+    assert int(core.w.max()) == 255 and n * 255 >= 0xFFFFFFFF
+    row_ptr = np.concatenate([core.row_ptr, np.full(n - core.n, core.row_ptr[-1], np.uint32)])
+    g = inputs.Graph(n, row_ptr, core.col, row_ptr, core.col, core.w, core.w, True, "sparse-wide")
+    ref = _ref(g, 0)
+    with ipg.Graph.from_inputs(g) as G:
+        _check(G, ref, 0, policy="forced", forced_mode="pull", pr_engine="blocked")
+        assert G.info()["bytes_blocked_layout"] == 0
