@@ -106,3 +106,23 @@ def test_in_edge_rows_wait_for_the_first_run_that_reads_them(relabel):
         for i in range(len(srcs)):
             assert np.array_equal(dist[i], ss[i]), i
         assert G.info()["bytes_graph"] == 2 * csr
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+def test_pinned_directed_weighted_renumbered(offset):
+    """Directed weighted graph from page-locked arrays, renumbered during creation:
+    the renumbering copy reads columns and weights from the host and counts the
+    in-degrees on the way (offset 0), or the arrays are copied first (offset 1, a
+    view the copy kernel cannot read at 16-byte alignment); SSSP on both pull engines,
+    PageRank and the in-degree maximum match the oracle."""
+    d = inputs.rmat_graph(12, weighted=True, seed=13)
+    ss, _ = oracle.sssp(d.n, d.row_ptr, d.col, d.w, source=3)
+    pr, _ = oracle.pagerank(d.n, d.row_ptr, d.col, T=30)
+    with ipg.Graph(d.n, _pin(d.row_ptr, offset), _pin(d.col, offset), _pin(d.w, offset), relabel=True) as G:
+        assert G.info()["max_in_degree"] == int(np.diff(d.t_ptr.astype(np.int64)).max())
+        for eng in ("gather", "blocked"):
+            G.run("sssp", source=3, policy="forced", forced_mode="pull", pr_engine=eng)
+            assert np.array_equal(G.values("sssp"), ss), eng
+        G.run("pagerank", policy="forced", forced_mode="pull")
+        got = G.values("pagerank").astype(np.float64)
+        assert float(np.max(np.abs(got - pr) / pr)) <= 1e-5
