@@ -617,6 +617,16 @@ __global__ void k_pb_tails(uint32_t* code, const uint2* tails, uint32_t nb, uint
         for (uint32_t e = tails[q].x; e < tails[q].y; ++e) code[e] = value;
 }
 
+// At build: the bin tails hold code 0 and destination 0 (every other entry belongs to a
+// run: the placement writes its destination, every scatter its code).
+__global__ void k_pb_tails_init(uint32_t* code, uint16_t* dst, const uint2* tails, uint32_t nb) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += gridDim.x * blockDim.x)
+        for (uint32_t e = tails[q].x; e < tails[q].y; ++e) {
+            code[e] = 0u;
+            dst[e] = 0;
+        }
+}
+
 // ---------------------------------------------------------------- layout build
 // Bin of a destination without a per-vertex table: tab[b] is the bin of vertex
 // min(b << sh, V - 1) (at most PB_TAB + 1 entries, in shared memory), so the bin of v
@@ -1137,29 +1147,28 @@ int build(ip_graph* g, cudaStream_t st, PbLayout** out) {
     PBK(pb_alloc(g, L, &d_big, V));
     PBK(pb_alloc(g, L, &d_hi, V));
     PBK(cuda_err(cudaMemsetAsync(d_hi, 0, sizeof(uint32_t) * V, st)));
-    // padding entries keep code 0 and destination 0: phase 1 never writes them
-    PBK(cuda_err(cudaMemsetAsync(d_dst, 0, sizeof(uint16_t) * std::max<uint64_t>(P_total, 1), st)));
-    PBK(cuda_err(cudaMemsetAsync(d_code, 0, sizeof(uint32_t) * std::max<uint64_t>(P_total, 1), st)));
-    if (nC)
-        k_pb_place<<<nC, PBP_THREADS, smem_place, st>>>(g->csr_off, g->csr_col, d_cs, d_abase, d_tab, sh, ntab,
-                                                        d_bstart, d_bbase, nb, d_M, d_O, d_runs, d_src, d_dst,
-                                                        g->csr_w, d_w8);
-    PBK(cuda_err(cudaGetLastError()));
-
-    // phase-2 tasks, one per bin, in bin order; the tail of every bin (entries after its runs)
+    // phase-2 tasks, one per bin, in bin order; the tail of every bin (entries after its
+    // runs, never written by the placement or a scatter) starts as code 0, destination 0
     std::vector<uint4> tasks(nb);
     std::vector<uint2> tails(nb);
     for (uint32_t q = 0; q < nb; ++q) {
         tasks[q] = make_uint4(bstart[q], bstart[q + 1] - bstart[q], bbase[q], bbase[q + 1]);
         tails[q] = make_uint2(bbase[q] + total[q], bbase[q + 1]);
     }
+    PBK(pb_alloc(g, L, &L->tails, nb));
+    PBK(cuda_err(cudaMemcpyAsync(L->tails, tails.data(), sizeof(uint2) * nb, cudaMemcpyHostToDevice, st)));
+    k_pb_tails_init<<<std::max<uint32_t>(1, (nb + 255) / 256), 256, 0, st>>>(d_code, d_dst, L->tails, nb);
+    if (nC)
+        k_pb_place<<<nC, PBP_THREADS, smem_place, st>>>(g->csr_off, g->csr_col, d_cs, d_abase, d_tab, sh, ntab,
+                                                        d_bstart, d_bbase, nb, d_M, d_O, d_runs, d_src, d_dst,
+                                                        g->csr_w, d_w8);
+    PBK(cuda_err(cudaGetLastError()));
+
     uint4* d_tasks;
     uint32_t* d_ctr;
     PBK(pb_alloc(g, L, &d_tasks, nb));
     PBK(pb_alloc(g, L, &d_ctr, 2));
-    PBK(pb_alloc(g, L, &L->tails, nb));
     PBK(cuda_err(cudaMemcpyAsync(d_tasks, tasks.data(), sizeof(uint4) * nb, cudaMemcpyHostToDevice, st)));
-    PBK(cuda_err(cudaMemcpyAsync(L->tails, tails.data(), sizeof(uint2) * nb, cudaMemcpyHostToDevice, st)));
     PBK(cuda_err(cudaMemsetAsync(d_ctr, 0, sizeof(uint32_t) * 2, st)));
     PBK(cuda_err(cudaStreamSynchronize(st)));
 
