@@ -189,13 +189,17 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- kernel byte models
 def launches_of(mode_seq, app, blocked=False):
-    """Kernels one run launches: init + selector, then per superstep the mode's kernels + selector."""
-    n = 2
+    """Kernels one run launches: superstep 0 (PageRank: k_pr_init; a vertex program:
+    k_ctl_init + k_init_prog) + the selector, then per superstep the mode's kernels +
+    the selector (blocked: the pull streams the blocked layout, two kernels)."""
+    n = 2 if app == "pagerank" else 3
     for m in mode_seq[1:]:
         if app == "pagerank":
             n += (3 if blocked else 2) if m == 2 else 3
+        elif m == 0:
+            n += 4  # compaction, push, apply, selector
         else:
-            n += 4 if m == 0 else 3
+            n += 4 if (m == 2 and blocked) else 3  # (scatter + accumulate | pull | push), apply, selector
     return n
 
 
@@ -414,7 +418,9 @@ def run_gpu(args, rank, world, local_rank):
             with torch.cuda.stream(stream):
                 ev[i][1].record(stream)
             msgs += int(a.messages.sum()) + int(b.messages.sum())
-            launches += launches_of(a.mode.tolist(), "pagerank", blocked=True) + launches_of(b.mode.tolist(), "hashmin")
+            hm_blocked = H.info()["bytes_blocked_layout"] > 0  # built at the start of a run that uses it
+            launches += (launches_of(a.mode.tolist(), "pagerank", blocked=True) +
+                         launches_of(b.mode.tolist(), "hashmin", blocked=hm_blocked))
             runs["pagerank"].append(a)
             runs["hashmin"].append(b)
         torch.cuda.synchronize()
