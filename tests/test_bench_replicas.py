@@ -92,3 +92,17 @@ def test_clock_summary_keeps_the_timed_region(tmp_path):
     s = c.summary()
     assert s["samples"] == 1 and s["sm_mhz"] == 2040 and s["reasons"] == ["hw_slowdown"]
     assert s["window"].startswith("nearest")
+
+
+def test_kernel_count_of_a_run():
+    """gpu_launches counts the library's kernels per run from the modes it ran:
+    PageRank, 30 blocked pulls: k_pr_init + selector, then scatter + accumulate +
+    selector per superstep; Hashmin: two superstep-0 kernels + selector, a blocked
+    pull = scatter + accumulate + apply + selector, a gather pull or a dense push =
+    3, a sparse push = compaction + push + apply + selector."""
+    import bench
+    assert bench.launches_of([0] + [2] * 30, "pagerank", blocked=True) == 2 + 30 * 3
+    assert bench.launches_of([0] + [2] * 30, "pagerank") == 2 + 30 * 2
+    modes = [0, 2, 2, 2, 1, 0, 0]
+    assert bench.launches_of(modes, "hashmin", blocked=True) == 3 + 3 * 4 + 3 + 4 + 4
+    assert bench.launches_of(modes, "hashmin") == 3 + 3 * 3 + 3 + 4 + 4
