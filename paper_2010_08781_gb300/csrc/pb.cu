@@ -69,7 +69,7 @@ constexpr size_t PB1_SMEM = (PB_MAXS + 1) * sizeof(uint32_t);
 // two chunks in flight per SM took 68.05 ms for T = 30 against 69.78 ms with three
 // (and 76.2 ms with one); the depth of loads in flight mattered less (4-12 groups within 0.7%)
 constexpr size_t PB1_SMEM_PR = 80 * 1024;
-constexpr size_t PB1_SMEM_MIN = PB1_SMEM;  // k_pbm_scatter's
+constexpr size_t PB1_SMEM_MIN = PB1_SMEM;  // k_pbm_scatter's (three CTAs per SM measured best there)
 constexpr size_t PB2_SMEM = PB_BIN_V * sizeof(uint32_t) + (size_t)PB_STAGES * PB_TILE * (4 + 2) +
                             PB_STAGES * (32 + 16);
 
@@ -477,7 +477,9 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
 // ---------------------------------------------------------------- min programs
 // The same layout and the same two phases for a vertex program whose combiner is
 // the uint32 minimum and whose message is the sender's value itself (Hashmin,
-// Fig. 9): the codes are the broadcast slots (the no-broadcast pattern for a vertex
+// Fig. 9; KIND PB_COPY_CODES) or the value plus the edge's weight (SSSP, Fig. 10;
+// PB_ADD_W8 with the entry's weight byte, PB_ADD_ONE on unweighted graphs): the codes
+// are the messages of the broadcasting senders (the no-broadcast pattern for a vertex
 // that did not broadcast, which also fills the padding entries and the bin tails,
 // so they change nothing), and a bin folds its codes with a shared-memory atomicMin
 // per destination. A destination whose minimum is a message is a recipient (no
