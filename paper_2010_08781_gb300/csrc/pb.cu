@@ -58,7 +58,7 @@ constexpr int PB1_THREADS = 512, PBB_THREADS = 512;
 constexpr int PBP_THREADS = 1024;
 constexpr size_t PBP_MIN_SMEM = 120 * 1024;
 // phase 1: groups of 4 entries per lane in flight (PageRank's scatter / the min programs')
-constexpr int PB1_LOADS_PR = 6, PB1_LOADS_MIN = 6;
+constexpr int PB1_LOADS_PR = 6, PB1_LOADS_MIN = 4;
 constexpr int PB_BATCH = 8;          // per-vertex loops (staging, compute()): loads in flight per thread
 constexpr int PB2_CONSUMERS = 24;    // phase 2: consumer warps (plus one producer warp)
 constexpr int PB_GROUPS = 2;        // phase 2: groups of 4 entries per consumer thread and stage
@@ -69,8 +69,8 @@ constexpr size_t PB1_SMEM = (PB_MAXS + 1) * sizeof(uint32_t);
 // two chunks in flight per SM took 68.05 ms for T = 30 against 69.78 ms with three
 // (and 76.2 ms with one); the depth of loads in flight mattered less (4-12 groups within 0.7%)
 constexpr size_t PB1_SMEM_PR = 80 * 1024;
-// k_pbm_scatter's: three CTAs per SM with 6 groups of loads in flight measured best at R-MAT 22
-// (Hashmin's pull 3% and SSSP's 1% faster than with 4; two CTAs per SM 4-5% slower)
+// k_pbm_scatter's: three CTAs per SM measured best; 6 groups of loads in flight instead of
+// 4 made R-MAT 22's pulls 1-3% faster but Hashmin at R-MAT 26 2-3% slower (kept at 4)
 constexpr size_t PB1_SMEM_MIN = PB1_SMEM;
 constexpr size_t PB2_SMEM = PB_BIN_V * sizeof(uint32_t) + (size_t)PB_STAGES * PB_TILE * (4 + 2) +
                             PB_STAGES * (32 + 16);
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(32 * (PB2_CONSUMERS + 1), 1) k_pb_accumulate(P
 // message of such a program equals the pattern): its mailbox gets the minimum and
 // its recipient bit is set, and the apply kernel runs compute() as after any pull.
 template <int KIND>
-__global__ void __launch_bounds__(PB1_THREADS, 3) k_pbm_scatter(Params P) {  // three CTAs per SM: 40 registers
+__global__ void __launch_bounds__(PB1_THREADS) k_pbm_scatter(Params P) {
     extern __shared__ uint32_t scode[];
     __shared__ uint32_t task, next_win;
     const PbDev& B = P.pb;
